@@ -11,7 +11,7 @@
  *  R2 random force: F^R = sigma w^R theta_ij e_ij / sqrt(dt); the 1/sqrt(dt)
  *     of the time-discretised Wiener increment is missing from Eq. random.
  *  R3 theta_ij: Philox4x32-10 (Salmon et al., SC'11) keyed by the box and
- *     counted by (min id, max id, step); Box-Muller on the top 24 bits of
+ *     counted by (min id, max id, step); Box-Muller on the top 23 bits of
  *     the first two output words, so theta_ij = theta_ji.
  *  R4 FENE: attractive, F_i = -H r_ij / (1 - (r/R0)^2); Eq. fene_force drops
  *     the minus sign that its commented -grad U states.
@@ -59,12 +59,13 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
   out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
-/* R3: two uniforms on the 2^24 grid (exact in any binary float of >= 24
- * bits), then Box-Muller. */
+/* R3: two uniforms u = (k + 1/2) 2^-23 from the top 23 bits k of a word
+ * (exactly representable in any binary float with a >= 24-bit significand,
+ * so every precision draws the same u), then Box-Muller. */
 double orc_theta_from_words(uint32_t x0, uint32_t x1) {
-  const double two_m24 = 1.0 / 16777216.0;
-  double u1 = ((double)(x0 >> 8) + 0.5) * two_m24;
-  double u2 = ((double)(x1 >> 8) + 0.5) * two_m24;
+  const double two_m23 = 1.0 / 8388608.0;
+  double u1 = ((double)(x0 >> 9) + 0.5) * two_m23;
+  double u2 = ((double)(x1 >> 9) + 0.5) * two_m23;
   return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
 }
 

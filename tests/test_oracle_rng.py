@@ -51,12 +51,12 @@ def test_theta_is_standard_normal():
 
 
 def test_box_muller_grid_extremes():
-    # u1, u2 live on the 2^-24 grid offset by half a cell: the smallest u1 gives
-    # the largest |theta| = sqrt(2 * 25 ln 2) and never log(0)
-    top = O.theta_from_words(0x000000FF, 0x00000000)
-    assert np.isclose(top, np.sqrt(-2 * np.log(0.5 / 2**24)) * np.cos(2 * np.pi * 0.5 / 2**24),
+    # u1, u2 live on the 2^-23 grid offset by half a cell: the smallest u1 gives
+    # the largest |theta| = sqrt(2 * 24 ln 2) and never log(0)
+    top = O.theta_from_words(0x000001FF, 0x00000000)
+    assert np.isclose(top, np.sqrt(-2 * np.log(0.5 / 2**23)) * np.cos(2 * np.pi * 0.5 / 2**23),
                       rtol=1e-14)
-    # the low 8 bits are dropped
-    assert O.theta_from_words(0x12345600, 0xABCDEF00) == O.theta_from_words(0x123456FF, 0xABCDEFFF)
+    # the low 9 bits are dropped
+    assert O.theta_from_words(0x12345600, 0xABCDEE00) == O.theta_from_words(0x123457FF, 0xABCDEFFF)
     # u1 = 1/2, u2 = 1/4 + half cell: theta = sqrt(2 ln 2) cos(pi/2 + eps) ~ 0
     assert abs(O.theta_from_words(0x80000000, 0x40000000)) < 1e-6
