@@ -26,6 +26,8 @@
  *     the length fraction of segment i->j inside the core over V_core.
  *     Sign: pi = -(sum m dv(x)dv + sum_{i<j} F_ij (x) r_ij)/V_core, i.e.
  *     f_ij of Eq. potential_stress is the force on j due to i.
+ *  R10 a bond at |r| >= R0 (Eq. fene_force undefined) is reported; its
+ *     stiffness is held at the (r/R0)^2 = 0.99 value so the run continues.
  */
 #include "lhmm_oracle.h"
 
@@ -178,14 +180,17 @@ static void dpd_pair_force(const orc_dpd_params* p, const orc_box* b, int i, int
   *hit = 1;
 }
 
-/* Eq. fene_force with the attractive sign (R4). Returns nonzero on |r| >= R0. */
+/* Eq. fene_force with the attractive sign (R4). Returns nonzero on |r| >= R0,
+ * where the spring is undefined; the run then continues with the spring
+ * stiffness held at its (r/R0)^2 = 0.99 value (R10) and the error reported. */
 static int fene_force(const orc_dpd_params* p, const double dr[3], double F[3]) {
   double r2 = dr[0] * dr[0] + dr[1] * dr[1] + dr[2] * dr[2];
   double x = r2 / (p->R0 * p->R0);
-  if (!(x < 1.0)) { F[0] = F[1] = F[2] = 0.0; return 1; }
+  int over = 0;
+  if (!(x < 1.0)) { x = 0.99; over = 1; }
   double c = -p->H_fene / (1.0 - x);
   F[0] = c * dr[0]; F[1] = c * dr[1]; F[2] = c * dr[2];
-  return 0;
+  return over;
 }
 
 static double lees_edwards_rate(const orc_dpd_params* p, const double L[9]) {

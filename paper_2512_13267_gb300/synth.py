@@ -62,6 +62,8 @@ def initial_box_state(edge, n_beads, seed, box_id=0, kBT=1.0, mass=1.0, L=None,
     imposed streaming profile (u = L r' about the box centre for AFBC,
     u_x = L_xy (y - Ly/2) for Lees-Edwards)."""
     edge = np.broadcast_to(np.asarray(edge, dtype=np.float64), (3,))
+    if n_beads == 0:
+        return np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32)
     rng = np.random.default_rng([int(seed), int(box_id), 0x5EED])
     n_side = int(np.ceil(n_beads ** (1.0 / 3.0) - 1e-9))
     while n_side ** 3 < n_beads:
