@@ -1,0 +1,306 @@
+"""Benchmark of the batched DPD micro step (the LHMM micro hot path).
+
+One step = one lhmm_micro_advance call that advances every box of the
+batched-microsolver workload (1024 AFBC boxes, edges uniform in {6..12},
+about 2.57M beads, 20 % of them in N_d = 10 FENE chains, per-box velocity
+gradients) by 100 DPD steps and returns per-box time-averaged IK stress.
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs its own
+batch of the same shape (weak scaling, no data-path collective).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+build) on a bounded sample of the same workload on the host cores.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DPD bead-steps/s (batched micro boxes)"
+UNIT = "bead-steps/s"
+MICRO_STEPS = 100
+# Algorithmic lane-operations per bead-step (each unique interacting pair
+# once, no rejected candidates); derivation in the design doc.
+PAIRS_PER_BEAD = 2.0 * np.pi / 3.0 * 3.0  # rho (4 pi / 3) rc^3 / 2 at rho = 3
+OPS_PER_PAIR = 136
+OPS_PER_BEAD = 35
+ALGO_OPS_PER_BEAD_STEP = PAIRS_PER_BEAD * OPS_PER_PAIR + OPS_PER_BEAD
+N_SM = 152
+LANES_PER_SM_CLK = 128
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def workload_desc(batch):
+    return {"workload": "batched micro step: %d AFBC DPD/FENE boxes, edge U{6..12} r_c, "
+                        "%d beads (rho 3, 20%% in N_d=10 chains), %d DPD steps per call"
+                        % (batch.n_boxes, batch.total_beads, MICRO_STEPS),
+            "boxes": batch.n_boxes, "beads": batch.total_beads, "micro_steps_per_step": MICRO_STEPS,
+            "l2": "flushed (256 MiB write) between timed steps"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, n in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(batch, budget_s=12.0, min_s=6.0, chunk_steps=5, n_boxes=24):
+    """FP64 oracle (OpenMP over boxes) on a fixed sample of the same workload.
+    Returns (bead-steps/s, threads, description)."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+    rng = np.random.default_rng(1234)
+    ids = np.sort(rng.choice(batch.n_boxes, size=min(n_boxes, batch.n_boxes), replace=False))
+    par = O.dpd_params(flow_mode=O.FLOW_AFBC, seed=2)
+    boxes = []
+    for b in ids:
+        sl = batch.box_slice(int(b))
+        ob = O.Box(batch.edges[b], batch.pos[sl], batch.vel[sl], int(batch.n_chains[b]),
+                   batch.chain_len, box_id=int(b))
+        O.compute_forces(par, ob, batch.L[b])
+        boxes.append(ob)
+    L = batch.L[ids].astype(np.float64)
+    beads = int(sum(b.n for b in boxes))
+    threads = O.max_threads()
+    done = 0
+    t0 = time.perf_counter()
+    while True:
+        O.advance_batch(par, boxes, L, chunk_steps, n_threads=threads)
+        done += chunk_steps
+        el = time.perf_counter() - t0
+        if el >= min_s or el >= budget_s:
+            break
+    rate = beads * done / el
+    desc = "%d of %d boxes (%d beads), %d DPD steps, %.1f s" % (len(ids), batch.n_boxes, beads,
+                                                                 done, el)
+    return rate, threads, desc
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2512_13267_gb300 import synth
+    batch = synth.batched_microsolver()
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+    rng = np.random.default_rng(1234)
+    ids = np.sort(rng.choice(batch.n_boxes, size=16, replace=False))
+    par = O.dpd_params(flow_mode=O.FLOW_AFBC, seed=2)
+    boxes = []
+    for b in ids:
+        sl = batch.box_slice(int(b))
+        ob = O.Box(batch.edges[b], batch.pos[sl], batch.vel[sl], int(batch.n_chains[b]),
+                   batch.chain_len, box_id=int(b))
+        O.compute_forces(par, ob, batch.L[b])
+        boxes.append(ob)
+    L = batch.L[ids].astype(np.float64)
+    beads = int(sum(b.n for b in boxes))
+    threads = O.max_threads()
+    steps_per = 10
+    for _ in range(args.warmup):
+        O.advance_batch(par, boxes, L, steps_per, n_threads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.advance_batch(par, boxes, L, steps_per, n_threads=threads)
+    el = time.perf_counter() - t0
+    value = beads * steps_per * args.steps / el
+    cfg = workload_desc(batch)
+    sample = ("each step: %d sampled boxes (%d beads) x %d DPD steps of the %d-box workload"
+              % (len(ids), beads, steps_per, batch.n_boxes))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg, "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--boxes", type=int, default=1024,
+                    help="boxes of the workload (a smaller case for profilers)")
+    ap.add_argument("--micro-steps", type=int, default=100, help="DPD steps per call")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2512_13267_gb300 import lhmm, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    lhmm.lib()
+
+    global MICRO_STEPS
+    MICRO_STEPS = args.micro_steps
+    batch = synth.batched_microsolver(n_boxes=args.boxes, seed=2 + rank)
+    params = lhmm.dpd_params(flow="afbc", seed=2 + rank)
+    micro = lhmm.Micro.from_batch(params, batch)
+    stream = torch.cuda.current_stream()
+    L = torch.from_numpy(batch.L).cuda()
+    stress = torch.zeros((batch.n_boxes, 6), dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+
+    micro.autotune(L, probe_steps=10)  # launch plan per size class (state restored)
+    for _ in range(max(args.warmup, 0)):
+        micro.advance(L, MICRO_STEPS, stress)
+    torch.cuda.synchronize()
+    micro.sync(raise_on_error=False)  # over-stretch under strong extension is reported below
+
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    evs = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        micro.advance(L, MICRO_STEPS, stress)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    times_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = float(sum(times_ms))
+    status, _ = micro.sync(raise_on_error=False)
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    bead_steps_rank = batch.total_beads * MICRO_STEPS * args.steps
+    value = bead_steps_rank * world / (max_ms / 1e3)
+
+    # end to end through the host-buffer entry point (pinned buffers)
+    L_pin = torch.from_numpy(batch.L).pin_memory()
+    st_pin = torch.zeros((batch.n_boxes, 6), dtype=torch.float64).pin_memory()
+    micro.advance_host(L_pin.numpy(), MICRO_STEPS, st_pin.numpy())
+    e2e_steps = max(2, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        micro.advance_host(L_pin.numpy(), MICRO_STEPS, st_pin.numpy())
+    e2e_s = time.perf_counter() - t0
+    e2e_val = batch.total_beads * MICRO_STEPS * e2e_steps * world / e2e_s
+
+    peaks, src = _peaks()
+    clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = N_SM * LANES_PER_SM_CLK * clk_mhz * 1e6 / 1e12  # T lane-ops/s
+    per_launch_ops = ALGO_OPS_PER_BEAD_STEP * batch.total_beads * MICRO_STEPS
+    launch_s = (total_ms / args.steps) / 1e3
+    achieved = per_launch_ops / launch_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+                "frac": achieved / alu_peak, "traffic": None,
+                "peak_source": "%d SMs x %d FP32/INT lanes x %.0f MHz (%s sm_max_mhz)"
+                               % (N_SM, LANES_PER_SM_CLK, clk_mhz, src),
+                "kernel": "micro_kernel", "algo_ops_per_bead_step": ALGO_OPS_PER_BEAD_STEP}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": workload_desc(batch), "roofline": roofline,
+            "e2e": {"value": e2e_val, "unit": UNIT,
+                    "h2d_bytes_per_step": int(L_pin.numel() * 4),
+                    "d2h_bytes_per_step": int(st_pin.numel() * 8)},
+            "gpu_launches": args.steps * len(micro.plan()),
+            "launch_plan": micro.plan(), "device_status": lhmm.status_string(status)}
+    if clk is not None:
+        line["clocks"] = clk
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, desc = cpu_oracle_rate(batch)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": desc}
+    micro.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,187 @@
+/*
+ * lhmm.h -- C ABI of the GB300 (sm_103a) LHMM hot path.
+ *
+ * The Lagrangian Heterogeneous Multiscale Method of arXiv 2512.13267 couples
+ * a macroscale SPH fluid to one microscale DPD/FENE polymer box per SPH
+ * particle.  Every macro step the SPH velocity gradient goes down to the
+ * boxes (Sec. 3.4, Eqs. macro_micro and micro_bc), each box advances k'
+ * DPD steps (Sec. 2.3, Eqs. motion..fene_force, coupling protocol Step 3)
+ * and returns its time-averaged Irving-Kirkwood polymer stress (Sec. 3.5,
+ * Eqs. IKtotal..potential_stress), scaled by alpha/lambda* (Eq. pip), to the
+ * SPH momentum equation (Eq. sph_continuity).
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers named *_dev are device pointers, *_host are host pointers.  The
+ *    caller owns them; the library never frees or retains them after the call.
+ *  - The library owns the handles and all of their internal device state.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls that take a stream only enqueue work and return; calls
+ *    documented as synchronous wait for their own work.
+ *  - Arguments are checked on the host; a bad argument returns LHMM_ERR_ARG
+ *    and enqueues nothing.  No call aborts, traps or prints.
+ *  - Errors detected on the device (bond over-stretch, NaN) are kept in a
+ *    per-box status word and reported by lhmm_micro_sync.
+ *  - Handles are not thread-safe: one host thread per handle at a time.
+ *  - Tensor layouts: a velocity gradient L is 9 floats, row-major,
+ *    L[3a+b] = du_a/dx_b (so the imposed streaming velocity is u = L r).  A
+ *    stress is 6 doubles in the order xx, yy, zz, xy, xz, yz.
+ */
+#ifndef LHMM_H
+#define LHMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LHMM_OK = 0,
+  LHMM_ERR_ARG = 1,             /* invalid argument, nothing enqueued */
+  LHMM_ERR_CUDA = 2,            /* a CUDA runtime call failed */
+  LHMM_ERR_OOM = 3,             /* device allocation failed */
+  LHMM_ERR_BOND_OVERSTRETCH = 4,/* a FENE bond reached |r| >= R0 (Eq. fene_force undefined) */
+  LHMM_ERR_CELL_OVERFLOW = 5,   /* a box outgrew its shared-memory plan */
+  LHMM_ERR_NAN = 6,             /* a non-finite bead velocity or force */
+  LHMM_ERR_TIMEOUT = 7,         /* a bounded device wait gave up */
+  LHMM_ERR_UNSUPPORTED = 8      /* a configuration this build does not run */
+} lhmm_status;
+
+/* per-box device status bits, as returned by lhmm_micro_sync */
+#define LHMM_BOX_BOND_OVERSTRETCH 1u
+#define LHMM_BOX_NAN 2u
+#define LHMM_BOX_CELL_OVERFLOW 4u
+
+/* imposed-flow treatment of the micro boxes */
+#define LHMM_FLOW_PERIODIC 0     /* plain periodic box, no imposed flow */
+#define LHMM_FLOW_LEES_EDWARDS 1 /* sliding-brick images for shear du_x/dy = L[1] */
+#define LHMM_FLOW_AFBC 2         /* arbitrary-flow boundary conditions (Sec. 4.1, Table 2) */
+
+/* DPD/FENE parameters (Sec. 2.3; Table 1 for the paper's melts).
+ * sigma should satisfy the FDT sigma^2 = 2 gamma kBT; it is not enforced. */
+typedef struct {
+  float a_ij;        /* conservative amplitude, Eq. conservative */
+  float gamma;       /* dissipative coefficient gamma^D, Eq. dissipative */
+  float sigma;       /* random amplitude sigma^R, Eq. random */
+  float kBT;         /* thermal energy (used for documentation/diagnostics) */
+  float rc;          /* cutoff radius; cells are >= rc wide */
+  float H_fene;      /* FENE spring constant, Eq. fene_force */
+  float R0;          /* FENE maximum bond extension */
+  float dt;          /* DPD time step */
+  float mass;        /* bead mass */
+  uint64_t seed;     /* key of the counter-based random stream */
+  int flow_mode;     /* LHMM_FLOW_* */
+  float afbc_core_frac; /* AFBC core width / box edge (Table 2: 24/76) */
+  float afbc_bc_frac;   /* AFBC BC shell width / box edge, per side (Table 2: 13/76) */
+  int dpd_on_bonded;    /* 1: DPD pair forces also act on bonded pairs (sum over all j != i) */
+  double alpha;         /* viscosity ratio alpha, Eq. ratios; output is scaled by alpha/lambda* */
+  double lambda_star;   /* time-scale ratio lambda*, Eq. ratios; input L is scaled by lambda* */
+} lhmm_dpd_params;
+
+/* A batch of independent boxes.  Box b has edges box_edge[3b..3b+2] (its
+ * beads live in [0, edge)), n_beads[b] beads with ids 0..n_beads[b]-1, and
+ * n_chains[b] FENE chains of chain_len consecutive ids starting at id 0
+ * (bonds (k, k+1) inside a chain); the remaining ids are solvent.  Beads of
+ * all boxes are concatenated in box order in every per-bead array. */
+typedef struct {
+  int n_boxes;
+  const float* box_edge; /* host, n_boxes x 3; every edge >= 3 rc */
+  const int* n_beads;    /* host, n_boxes; 0 <= n < 65536 */
+  const int* n_chains;   /* host, n_boxes; n_chains * chain_len <= n_beads */
+  int chain_len;         /* N_d >= 2 (ignored when every n_chains is 0) */
+} lhmm_batch_desc;
+
+typedef struct lhmm_micro_s* lhmm_micro_t;
+
+const char* lhmm_status_string(lhmm_status s);
+
+/* Create a batch of micro-domains from initial bead states (host,
+ * total_beads x 3: absolute positions inside each box as double, velocities
+ * as float), and
+ * compute the initial forces F(0) under the velocity gradients L0_host (host,
+ * n_boxes x 9, or NULL for zero; Lees-Edwards boxes need it for the velocity
+ * jump of their sliding images).  Synchronous.  Allocates all device state. */
+lhmm_status lhmm_micro_create(const lhmm_dpd_params* params, const lhmm_batch_desc* batch,
+                              const double* pos0_host, const float* vel0_host,
+                              const float* L0_host, void* stream, lhmm_micro_t* out);
+lhmm_status lhmm_micro_destroy(lhmm_micro_t h);
+
+/* Advance boxes by n_steps velocity-Verlet DPD steps (coupling protocol,
+ * Step 3) under their velocity gradients, and write the time average over
+ * those steps of the IK stress (Eqs. IKtotal..potential_stress, sampled after
+ * each full step) times alpha/lambda* (Eq. pip).
+ *   L_dev         device, n_boxes x 9 float, indexed by box id; scaled by
+ *                 lambda* inside (Eq. micro_bc).  PERIODIC ignores it,
+ *                 LEES_EDWARDS reads only L[1] = du_x/dy.
+ *   box_idx_dev   device, n_active box ids to advance, or NULL for all boxes
+ *                 (then n_active must equal n_boxes); ids must be distinct.
+ *   n_steps       >= 0 (k' of the coupling interval)
+ *   stress_dev    device, n_boxes x 6 double, rows indexed by box id; only
+ *                 the advanced boxes' rows are written.
+ *   stress_sq_dev device, n_boxes x 6 double or NULL: time average of the
+ *                 square of each per-step sample (for standard errors).
+ * Asynchronous on `stream`.  Device-side errors surface in lhmm_micro_sync. */
+lhmm_status lhmm_micro_advance(lhmm_micro_t h, const float* L_dev, const int* box_idx_dev,
+                               int n_active, int n_steps, double* stress_dev,
+                               double* stress_sq_dev, void* stream);
+
+/* The same over host buffers: copies L_host (n_boxes x 9) in, advances all
+ * boxes, copies stress (n_boxes x 6) and optionally stress_sq back, and waits
+ * for the stream.  Synchronous.  Uses staging buffers owned by the handle. */
+lhmm_status lhmm_micro_advance_host(lhmm_micro_t h, const float* L_host, int n_steps,
+                                    double* stress_host, double* stress_sq_host, void* stream);
+
+/* Wait for the handle's stream work, read the per-box status words into
+ * box_status_host (n_boxes uint32, or NULL), clear them, and return the first
+ * error they hold (LHMM_ERR_BOND_OVERSTRETCH, LHMM_ERR_NAN,
+ * LHMM_ERR_CELL_OVERFLOW) or LHMM_OK.  Synchronous. */
+lhmm_status lhmm_micro_sync(lhmm_micro_t h, uint32_t* box_status_host);
+
+/* Copy one box's state to the host: absolute positions (n x 3 double; the
+ * library keeps FP32 offsets inside cells, and a double holds cell origin plus
+ * offset exactly), velocities and the forces of the current state (the ones
+ * the next half kick uses), its completed step count and Lees-Edwards offset.
+ * Any pointer may be NULL.  Synchronous. */
+lhmm_status lhmm_micro_get_state(lhmm_micro_t h, int box, double* pos_host, float* vel_host,
+                                 float* force_host, uint64_t* step, float* le_offset);
+/* Overwrite one box's state (checkpoint/resume).  pos/vel/force are required;
+ * the random stream continues from `step`, so a state saved with get_state
+ * resumes bit for bit.  Synchronous. */
+lhmm_status lhmm_micro_set_state(lhmm_micro_t h, int box, const double* pos_host,
+                                 const float* vel_host, const float* force_host, uint64_t step,
+                                 float le_offset);
+
+/* Sizes of the batch. */
+lhmm_status lhmm_micro_info(lhmm_micro_t h, int* n_boxes, int64_t* total_beads, int* max_beads);
+
+/* Launch plan (not in the paper; the batching layer of this library).  Boxes
+ * are grouped into size classes of similar bead count; each class runs as one
+ * launch on a stream of its own (forked from and joined back into the caller's
+ * stream), with a shared-memory plan sized to its largest box and one of
+ * LHMM_MICRO_N_VARIANTS kernel variants (threads per block x resident blocks
+ * per SM).  A subset advance (box_idx_dev != NULL) is one launch sized to the
+ * largest box of the batch. */
+#define LHMM_MICRO_N_VARIANTS 5
+
+/* Time every variant on probe_steps steps of each class's boxes under L_dev
+ * (device, n_boxes x 9) and keep the fastest per class; results are cached
+ * per (largest box, cells, flow mode, device) for the process.  The bead state
+ * is saved before and restored after, so the batch does not advance.  The
+ * choice changes floating-point summation order, so a run is bit-reproducible
+ * for a fixed plan (see lhmm_micro_set_variant).  Synchronous; allocates a
+ * temporary copy of the bead state. */
+lhmm_status lhmm_micro_autotune(lhmm_micro_t h, const float* L_dev, int probe_steps, void* stream);
+
+/* Read the plan: the number of classes, and for the first `cap` classes their
+ * box count, largest box, threads per block and resident blocks per SM. */
+lhmm_status lhmm_micro_plan(lhmm_micro_t h, int* n_classes, int cap, int* class_boxes,
+                            int* class_max_beads, int* class_threads, int* class_min_blocks);
+
+/* Pin the kernel variant (0..LHMM_MICRO_N_VARIANTS-1) of one class.  Returns
+ * LHMM_ERR_UNSUPPORTED if that variant's shared-memory plan does not fit. */
+lhmm_status lhmm_micro_set_variant(lhmm_micro_t h, int cls, int variant);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LHMM_H */

@@ -1,0 +1,1233 @@
+// micro.cu -- batched DPD/FENE micro-domains of the LHMM (arXiv 2512.13267,
+// Sec. 2.3 and 3.4-3.5, coupling protocol Steps 2-4) on sm_103a.
+//
+// Design: one thread block owns one box for a whole lhmm_micro_advance call.
+// The box's state (cell-relative FP32 positions, velocities, forces, cell ids)
+// is loaded once with float4 loads, stays in shared memory for all k' steps,
+// and is written back once, so HBM traffic is amortised over k' and the
+// kernel is bound by on-chip arithmetic.  Every step the block
+//   A  half-kicks and drifts its beads, re-normalising cell-relative offsets
+//      and applying Lees-Edwards re-entry (Sec. 2.3 VV; coupling Step 3);
+//   B  rebuilds a counting-sort cell list (cells >= rc wide) with a
+//      deterministic order inside each cell;
+//   C  sums DPD conservative, dissipative and random pair forces (Eqs.
+//      conservative, dissipative, random) over the 27 neighbour cells plus the
+//      FENE bonds (Eq. fene_force), accumulating the pair virial of the IK
+//      potential stress (Eq. potential_stress) with the core bond fraction;
+//   D  half-kicks, imposes v = lambda* L r' on the AFBC BC shell (Eq.
+//      micro_bc), accumulates the IK kinetic stress (Eq. kinetic_stress) and
+//      block-reduces the step's stress; the time average (N'_t = k') is kept
+//      in FP64.
+// Each pair is evaluated from both sides (no atomics, no cross-thread
+// writes), which keeps the force sums bit-reproducible.  The random term
+// theta_ij = theta_ji comes from Philox4x32-10 keyed by the box and counted
+// by (min id, max id, step), so it is identical from both sides and across
+// runs, and a checkpointed state resumes bit for bit.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "lhmm_common.cuh"
+
+namespace {
+
+struct BoxInfo {
+  long long off;      // first bead of the box in the flat arrays
+  int n;              // beads
+  int n_poly;         // beads in chains (n_chains * chain_len)
+  int nc[3];          // cells per axis (>= 3)
+  int ncell;
+  float w[3];         // cell widths (>= rc)
+  float winv[3];
+  float len[3];       // periodic lengths nc * w
+  float half_core[3]; // AFBC core half widths
+  float half_bc[3];   // AFBC BC-shell outer half widths
+  float inv_vcore;    // 1 / volume over which IK averages
+};
+
+struct BoxState {
+  unsigned long long step;  // completed steps; keys the random stream
+  float le_offset;          // Lees-Edwards image offset in x, [0, len_x)
+  unsigned status;          // LHMM_BOX_* bits
+};
+
+struct MicroArgs {
+  const BoxInfo* boxes;
+  BoxState* state;
+  float4* pos;  // (ox, oy, oz, cell id as int bits)
+  float4* vel;
+  float4* frc;
+  const int* list;  // blocks -> box ids
+  const float* L;   // n_boxes x 9
+  double* stress;
+  double* stress_sq;
+  int n_steps;
+  int init_forces;
+  float a, gamma, sig_dt, rc, rc2, rcinv, H, R0, inv_R0sq, dt, hdt_m, mass, lambda_star;
+  double out_scale;
+  unsigned seed_lo, seed_hi;
+  int flow, dpd_on_bonded, chain_len;
+  int max_beads, max_cells;
+  int n_boxes;
+};
+
+constexpr int kRedFloats = 192;  // 6 x 32 warps, also scan scratch
+constexpr int kQueue = 64;       // pair-queue entries per warp
+
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// Shared-memory plan of a box of up to N beads and C cells, T threads.
+__host__ __device__ inline size_t micro_smem_bytes(int N, int C, int T) {
+  size_t b = 9 * sizeof(float) * (size_t)N;    // offsets, velocities, forces (SoA)
+  b += 2 * sizeof(unsigned short) * (size_t)N;  // cell id per bead, sorted slot -> bead
+  b = align16(b);
+  b += sizeof(unsigned short) * (size_t)(C + 1); // cell start offsets
+  b = align16(b);
+  b += sizeof(unsigned short) * (size_t)(C + 1); // cell counters (packed in 32-bit words)
+  b = align16(b);
+  b += sizeof(unsigned long long) * (size_t)kQueue * (T / 32);  // pair queues
+  b += sizeof(float) * kRedFloats;
+  return b;
+}
+
+__device__ __forceinline__ int wrapi(int c, int n) {
+  c += (c < 0) ? n : 0;
+  c -= (c >= n) ? n : 0;
+  return c;
+}
+
+// Length fraction of segment a->b inside the open box |x_k| < h[k]: the IK
+// bond function for a uniform weight on the core (times V_core).
+__device__ __forceinline__ float seg_fraction(float ax, float ay, float az, float bx, float by,
+                                              float bz, const float* h) {
+  float lo = 0.f, hi = 1.f;
+  const float a[3] = {ax, ay, az}, d[3] = {bx - ax, by - ay, bz - az};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (d[k] == 0.f) {
+      if (!(fabsf(a[k]) < h[k])) return 0.f;
+      continue;
+    }
+    const float inv = 1.f / d[k];
+    const float s1 = (-h[k] - a[k]) * inv, s2 = (h[k] - a[k]) * inv;
+    lo = fmaxf(lo, fminf(s1, s2));
+    hi = fminf(hi, fmaxf(s1, s2));
+  }
+  return hi > lo ? hi - lo : 0.f;
+}
+
+// A queued pair: bead i, bead j, the image of j relative to i as neighbour
+// cell offsets (x may exceed one cell in a Lees-Edwards shifted row), the IK
+// bond-weight mode of i and the Lees-Edwards crossing of the row.
+__device__ __forceinline__ unsigned long long pack_pair(int i, int j, int dcx, int dy, int dz,
+                                                        int ikm, int cross) {
+  return static_cast<unsigned long long>(i) | (static_cast<unsigned long long>(j) << 16) |
+         (static_cast<unsigned long long>(dcx & 0xff) << 32) |
+         (static_cast<unsigned long long>(dy + 1) << 40) |
+         (static_cast<unsigned long long>(dz + 1) << 42) |
+         (static_cast<unsigned long long>(ikm) << 44) |
+         (static_cast<unsigned long long>(cross) << 46);
+}
+
+struct BoxView {
+  float *ox, *oy, *oz, *vx, *vy, *vz, *fx, *fy, *fz;
+  unsigned short *cellid, *perm, *cstart;
+};
+
+// Decode a linear cell index (exact for index < 2^16 in FP32 arithmetic).
+__device__ __forceinline__ void cell_coords(int c, int nx, int nxy, float inx, float inxy, int& cx,
+                                            int& cy, int& cz) {
+  cz = __float2int_rd((static_cast<float>(c) + 0.5f) * inxy);
+  const int rem = c - cz * nxy;
+  cy = __float2int_rd((static_cast<float>(rem) + 0.5f) * inx);
+  cx = rem - cy * nx;
+}
+
+template <int T, int MINB>
+__global__ void __launch_bounds__(T, MINB) micro_kernel(const MicroArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ BoxInfo sB;
+  __shared__ float sL[9];
+  constexpr int NW = T / 32;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int bid = A.list[blockIdx.x];
+  if (bid < 0 || bid >= A.n_boxes) return;  // whole block leaves together
+  if (tid == 0) sB = A.boxes[bid];
+  if (tid < 9) sL[tid] = A.lambda_star * A.L[9 * bid + tid];
+  __syncthreads();
+  const int N = sB.n, C = sB.ncell;
+  const int nx = sB.nc[0], ny = sB.nc[1], nz = sB.nc[2], nxy = nx * ny;
+  const float inx = 1.f / static_cast<float>(nx), inxy = 1.f / static_cast<float>(nxy);
+  const float wx = sB.w[0], wy = sB.w[1], wz = sB.w[2];
+
+  // carve shared memory (same plan as micro_smem_bytes)
+  const int NM = A.max_beads, CM = A.max_cells;
+  BoxView S;
+  S.ox = reinterpret_cast<float*>(smem);
+  S.oy = S.ox + NM;
+  S.oz = S.oy + NM;
+  S.vx = S.oz + NM;
+  S.vy = S.vx + NM;
+  S.vz = S.vy + NM;
+  S.fx = S.vz + NM;
+  S.fy = S.fx + NM;
+  S.fz = S.fy + NM;
+  S.cellid = reinterpret_cast<unsigned short*>(S.fz + NM);
+  S.perm = S.cellid + NM;
+  size_t b = align16(9 * sizeof(float) * (size_t)NM + 2 * sizeof(unsigned short) * (size_t)NM);
+  S.cstart = reinterpret_cast<unsigned short*>(smem + b);
+  b = align16(b + sizeof(unsigned short) * (size_t)(CM + 1));
+  unsigned* cnt32 = reinterpret_cast<unsigned*>(smem + b);  // two 16-bit counters per word
+  const unsigned short* cnt16 = reinterpret_cast<const unsigned short*>(cnt32);
+  b = align16(b + sizeof(unsigned short) * (size_t)(CM + 1));
+  unsigned long long* queue = reinterpret_cast<unsigned long long*>(smem + b) + kQueue * warp;
+  b += sizeof(unsigned long long) * (size_t)kQueue * NW;
+  float* red = reinterpret_cast<float*>(smem + b);
+  float *ox = S.ox, *oy = S.oy, *oz = S.oz, *vx = S.vx, *vy = S.vy, *vz = S.vz;
+  float *fx = S.fx, *fy = S.fy, *fz = S.fz;
+  unsigned short *cellid = S.cellid, *perm = S.perm, *cstart = S.cstart;
+
+  const long long off = sB.off;
+  for (int i = tid; i < N; i += T) {
+    const float4 p = A.pos[off + i], v = A.vel[off + i], f = A.frc[off + i];
+    ox[i] = p.x; oy[i] = p.y; oz[i] = p.z;
+    cellid[i] = static_cast<unsigned short>(__float_as_int(p.w));
+    vx[i] = v.x; vy[i] = v.y; vz[i] = v.z;
+    fx[i] = f.x; fy[i] = f.y; fz[i] = f.z;
+  }
+
+  const bool le = A.flow == LHMM_FLOW_LEES_EDWARDS;
+  const bool afbc = A.flow == LHMM_FLOW_AFBC;
+  const float gdot = sL[1];                      // LE shear rate (already x lambda*)
+  const float vjump = gdot * sB.len[1];          // velocity of the image above
+  const float le_inc = vjump * A.dt;             // image offset advance per step
+  const unsigned long long step0 = A.state[bid].step;
+  const float le0 = A.state[bid].le_offset;
+  const uint32_t k0 = A.seed_lo ^ static_cast<uint32_t>(bid), k1 = A.seed_hi;
+  const float hx = 0.5f * sB.len[0], hy = 0.5f * sB.len[1], hz = 0.5f * sB.len[2];
+  const unsigned lt_mask = (1u << lane) - 1u;
+  unsigned status = 0;
+  double acc_sum = 0.0, acc_sq = 0.0;  // threads 0..5 own one stress component each
+
+  const int total_steps = A.init_forces ? 1 : A.n_steps;
+  for (int s = 0; s < total_steps; ++s) {
+    const bool kick = !A.init_forces;
+    const unsigned long long step = kick ? step0 + s + 1 : step0;
+    const uint32_t st_lo = static_cast<uint32_t>(step), st_hi = static_cast<uint32_t>(step >> 32);
+    float le_off = 0.f;
+    if (le) {
+      le_off = kick ? le0 + static_cast<float>(s + 1) * le_inc : le0;
+      le_off -= floorf(le_off / sB.len[0]) * sB.len[0];
+      if (le_off >= sB.len[0]) le_off -= sB.len[0];
+    }
+    // ---- A: half kick + drift + cell re-normalisation
+    if (kick) {
+      for (int i = tid; i < N; i += T) {
+        float v0 = vx[i] + A.hdt_m * fx[i];
+        float v1 = vy[i] + A.hdt_m * fy[i];
+        float v2 = vz[i] + A.hdt_m * fz[i];
+        float o0 = ox[i] + A.dt * v0, o1 = oy[i] + A.dt * v1, o2 = oz[i] + A.dt * v2;
+        int cx, cy, cz;
+        cell_coords(cellid[i], nx, nxy, inx, inxy, cx, cy, cz);
+        if (o1 < 0.f || o1 >= wy) {
+          const int k = static_cast<int>(floorf(o1 * sB.winv[1]));
+          o1 -= static_cast<float>(k) * wy;
+          cy += k;
+          if (o1 < 0.f) o1 = 0.f;
+          if (o1 >= wy) { o1 -= wy; cy += 1; }
+          if (cy >= ny || cy < 0) {
+            const int up = cy >= ny;
+            cy += up ? -ny : ny;
+            if (le) {  // re-enter through the sliding image: shift x, jump v_x
+              o0 += up ? -le_off : le_off;
+              v0 += up ? -vjump : vjump;
+            }
+          }
+          if (cy < 0 || cy >= ny) {  // moved more than a box in one step
+            cy %= ny;
+            if (cy < 0) cy += ny;
+            status |= LHMM_BOX_NAN;
+          }
+        }
+        if (o0 < 0.f || o0 >= wx) {
+          const int k = static_cast<int>(floorf(o0 * sB.winv[0]));
+          o0 -= static_cast<float>(k) * wx;
+          cx += k;
+          if (o0 < 0.f) o0 = 0.f;
+          if (o0 >= wx) { o0 -= wx; cx += 1; }
+          cx %= nx;
+          if (cx < 0) cx += nx;
+        }
+        if (o2 < 0.f || o2 >= wz) {
+          const int k = static_cast<int>(floorf(o2 * sB.winv[2]));
+          o2 -= static_cast<float>(k) * wz;
+          cz += k;
+          if (o2 < 0.f) o2 = 0.f;
+          if (o2 >= wz) { o2 -= wz; cz += 1; }
+          cz %= nz;
+          if (cz < 0) cz += nz;
+        }
+        ox[i] = o0; oy[i] = o1; oz[i] = o2;
+        vx[i] = v0; vy[i] = v1; vz[i] = v2;
+        cellid[i] = static_cast<unsigned short>(cx + nx * (cy + ny * cz));
+      }
+    }
+    for (int c = tid; c < (C + 1) / 2; c += T) cnt32[c] = 0u;  // counters 0..C-1
+    __syncthreads();
+    // ---- B: counting sort by cell
+    for (int i = tid; i < N; i += T) {
+      const int c = cellid[i];
+      atomicAdd(&cnt32[c >> 1], (c & 1) ? 65536u : 1u);
+    }
+    __syncthreads();
+    {
+      const int per = (C + T - 1) / T;
+      const int c0 = min(tid * per, C), c1 = min(c0 + per, C);
+      int local = 0;
+      for (int c = c0; c < c1; ++c) local += cnt16[c];
+      int x = local;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+      }
+      int* scan = reinterpret_cast<int*>(red);
+      if (lane == 31) scan[warp] = x;
+      __syncthreads();
+      if (warp == 0) {
+        int y = lane < NW ? scan[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int z = __shfl_up_sync(FULL, y, o);
+          if (lane >= o) y += z;
+        }
+        if (lane < NW) scan[lane] = y;
+      }
+      __syncthreads();
+      int run = (warp > 0 ? scan[warp - 1] : 0) + x - local;
+      for (int c = c0; c < c1; ++c) {
+        cstart[c] = static_cast<unsigned short>(run);
+        run += cnt16[c];
+      }
+      if (tid == 0) cstart[C] = static_cast<unsigned short>(scan[NW - 1]);
+    }
+    __syncthreads();
+    for (int c = tid; c < (C + 1) / 2; c += T) cnt32[c] = 0u;  // counters 0..C-1
+    __syncthreads();
+    for (int i = tid; i < N; i += T) {
+      const int c = cellid[i];
+      const unsigned old = atomicAdd(&cnt32[c >> 1], (c & 1) ? 65536u : 1u);
+      const int rank = (c & 1) ? static_cast<int>(old >> 16) : static_cast<int>(old & 0xffffu);
+      perm[cstart[c] + rank] = static_cast<unsigned short>(i);
+    }
+    __syncthreads();
+    for (int c = tid; c < C; c += T) {  // ascending ids inside each cell
+      const int s0 = cstart[c], s1 = cstart[c + 1];
+      for (int p = s0 + 1; p < s1; ++p) {
+        const unsigned short key = perm[p];
+        int q = p - 1;
+        while (q >= s0 && perm[q] > key) {
+          perm[q + 1] = perm[q];
+          --q;
+        }
+        perm[q + 1] = key;
+      }
+    }
+    __syncthreads();
+
+    // ---- C: forces and pair virial.  Each lane owns one bead per round and
+    // scans its 27 neighbour cells (9 rows of 3 x-cells, each row one or two
+    // contiguous slot ranges); pairs inside r_c go to the warp's queue and are
+    // evaluated 32 at a time with every lane busy.
+    float W[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    auto eval_pair = [&](unsigned long long e) {
+      const int i = static_cast<int>(e & 0xffffu), j = static_cast<int>((e >> 16) & 0xffffu);
+      const int dcx = static_cast<int>(static_cast<signed char>((e >> 32) & 0xffu));
+      const int dy = static_cast<int>((e >> 40) & 3u) - 1, dz = static_cast<int>((e >> 42) & 3u) - 1;
+      const int ikm = static_cast<int>((e >> 44) & 3u), cross = static_cast<int>((e >> 46) & 3u);
+      const float sx = cross == 1 ? le_off : (cross == 2 ? -le_off : 0.f);
+      const float dvs = cross == 1 ? -vjump : (cross == 2 ? vjump : 0.f);
+      const float rx = (-static_cast<float>(dcx) * wx - sx) + (ox[i] - ox[j]);
+      const float ry = -static_cast<float>(dy) * wy + (oy[i] - oy[j]);
+      const float rz = -static_cast<float>(dz) * wz + (oz[i] - oz[j]);
+      const float r2 = rx * rx + ry * ry + rz * rz;
+      const float rinv = rsqrtf(r2);
+      const float r = r2 * rinv;
+      const float wR = 1.f - r * A.rcinv;
+      const float dvx = vx[i] - vx[j] + dvs, dvy = vy[i] - vy[j], dvz = vz[i] - vz[j];
+      const float ev = (rx * dvx + ry * dvy + rz * dvz) * rinv;
+      const uint2 rr = lhmm::philox4x32_10_xy(static_cast<uint32_t>(min(i, j)),
+                                              static_cast<uint32_t>(max(i, j)), st_lo, st_hi, k0, k1);
+      const float th = lhmm::gauss_from_words(rr.x, rr.y);
+      const float f = A.a * wR - A.gamma * wR * wR * ev + A.sig_dt * wR * th;
+      const float fr = f * rinv;
+      atomicAdd(&fx[i], fr * rx);
+      atomicAdd(&fy[i], fr * ry);
+      atomicAdd(&fz[i], fr * rz);
+      if (ikm) {
+        float wgt = 0.5f * fr;
+        if (ikm == 2) {
+          int cx, cy, cz;
+          cell_coords(cellid[i], nx, nxy, inx, inxy, cx, cy, cz);
+          const float rpx = static_cast<float>(cx) * wx + ox[i] - hx;
+          const float rpy = static_cast<float>(cy) * wy + oy[i] - hy;
+          const float rpz = static_cast<float>(cz) * wz + oz[i] - hz;
+          wgt *= seg_fraction(rpx, rpy, rpz, rpx - rx, rpy - ry, rpz - rz, sB.half_core);
+        }
+        W[0] += wgt * rx * rx;
+        W[1] += wgt * ry * ry;
+        W[2] += wgt * rz * rz;
+        W[3] += wgt * rx * ry;
+        W[4] += wgt * rx * rz;
+        W[5] += wgt * ry * rz;
+      }
+    };
+
+    int count = 0;  // warp-uniform queue fill
+    const int rounds = (N + T - 1) / T;
+    for (int rd = 0; rd < rounds; ++rd) {
+      const int k = tid + rd * T;
+      const bool own = k < N;
+      const int i = own ? perm[k] : 0;
+      int cx = 0, cy = 0, cz = 0, ikm = 1;
+      float xi = 0.f, yi = 0.f, zi = 0.f;
+      if (own) {
+        cell_coords(cellid[i], nx, nxy, inx, inxy, cx, cy, cz);
+        xi = ox[i]; yi = oy[i]; zi = oz[i];
+        const float rpx = static_cast<float>(cx) * wx + xi - hx;
+        const float rpy = static_cast<float>(cy) * wy + yi - hy;
+        const float rpz = static_cast<float>(cz) * wz + zi - hz;
+        if (afbc) {  // a pair segment reaches at most rc from bead i (max norm)
+          const float m = fmaxf(fabsf(rpx) - sB.half_core[0],
+                                fmaxf(fabsf(rpy) - sB.half_core[1], fabsf(rpz) - sB.half_core[2]));
+          ikm = (m >= A.rc) ? 0 : ((m < -A.rc) ? 1 : 2);
+        }
+        float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+        // FENE bonds (k, k+1) inside a chain, attractive (Eq. fene_force)
+        if (i < sB.n_poly) {
+#pragma unroll
+          for (int side = 0; side < 2; ++side) {
+            const int j = side == 0 ? i - 1 : i + 1;
+            const bool ok = side == 0 ? (i % A.chain_len) != 0 : ((i + 1) % A.chain_len) != 0;
+            if (!ok) continue;
+            int cxj, cyj, czj;
+            cell_coords(cellid[j], nx, nxy, inx, inxy, cxj, cyj, czj);
+            float rx = static_cast<float>(cx - cxj) * wx + (xi - ox[j]);
+            float ry = static_cast<float>(cy - cyj) * wy + (yi - oy[j]);
+            float rz = static_cast<float>(cz - czj) * wz + (zi - oz[j]);
+            if (ry > hy) {
+              ry -= sB.len[1];
+              if (le) rx -= le_off;
+            } else if (ry < -hy) {
+              ry += sB.len[1];
+              if (le) rx += le_off;
+            }
+            rx -= sB.len[0] * rintf(rx / sB.len[0]);
+            if (rz > hz) rz -= sB.len[2];
+            else if (rz < -hz) rz += sB.len[2];
+            float x = (rx * rx + ry * ry + rz * rz) * A.inv_R0sq;
+            if (!(x < 1.f)) {
+              status |= LHMM_BOX_BOND_OVERSTRETCH;
+              x = 0.99f;
+            }
+            const float cf = -A.H / (1.f - x);
+            Fx += cf * rx;
+            Fy += cf * ry;
+            Fz += cf * rz;
+            float wgt = 0.5f * cf;
+            if (afbc) {  // a bond is shorter than R0
+              const float m = fmaxf(fabsf(rpx) - sB.half_core[0],
+                                    fmaxf(fabsf(rpy) - sB.half_core[1], fabsf(rpz) - sB.half_core[2]));
+              if (m >= A.R0) wgt = 0.f;
+              else if (m >= -A.R0)
+                wgt *= seg_fraction(rpx, rpy, rpz, rpx - rx, rpy - ry, rpz - rz, sB.half_core);
+            }
+            W[0] += wgt * rx * rx;
+            W[1] += wgt * ry * ry;
+            W[2] += wgt * rz * rz;
+            W[3] += wgt * rx * ry;
+            W[4] += wgt * rx * rz;
+            W[5] += wgt * ry * rz;
+          }
+        }
+        fx[i] = Fx;
+        fy[i] = Fy;
+        fz[i] = Fz;
+      }
+      __syncwarp();
+      for (int row = 0; row < 9; ++row) {
+        const int dz = row / 3 - 1, dy = row % 3 - 1;
+        int len1 = 0, len2 = 0, s1 = 0, s2 = 0, w1 = 0, w2 = 0, u1 = 0, u2 = 0, cross = 0;
+        int rowbase = 0;
+        float sxr = 0.f;
+        if (own) {
+          const int z = wrapi(cz + dz, nz);
+          int y = cy + dy;
+          if (y < 0) {
+            y += ny;
+            if (le) { cross = 2; sxr = -le_off; }
+          } else if (y >= ny) {
+            y -= ny;
+            if (le) { cross = 1; sxr = le_off; }
+          }
+          rowbase = nx * (y + ny * z);
+          int ulo = cx - 1, uhi = cx + 1;
+          if (cross) {  // images slide by sxr: cells covering x_i - sxr +- rc
+            const float xt = static_cast<float>(cx) * wx + xi - sxr;
+            ulo = static_cast<int>(floorf((xt - A.rc) * sB.winv[0]));
+            uhi = min(static_cast<int>(floorf((xt + A.rc) * sB.winv[0])), ulo + 2);
+          }
+          const int wlo = ((ulo % nx) + nx) % nx, whi = ((uhi % nx) + nx) % nx;
+          const bool single = (wlo <= whi) && (whi - wlo == uhi - ulo);
+          w1 = wlo;
+          u1 = ulo;
+          s1 = cstart[rowbase + wlo];
+          len1 = cstart[rowbase + (single ? whi : nx - 1) + 1] - s1;
+          if (!single) {
+            w2 = 0;
+            u2 = uhi - whi;
+            s2 = cstart[rowbase];
+            len2 = cstart[rowbase + whi + 1] - s2;
+          }
+        }
+        const int len = len1 + len2;
+        const int lmax = __reduce_max_sync(FULL, len);
+        for (int t = 0; t < lmax; ++t) {
+          bool hit = false;
+          unsigned long long ent = 0ull;
+          if (t < len) {
+            const bool first = t < len1;
+            const int q = first ? s1 + t : s2 + (t - len1);
+            const int j = perm[q];
+            const int cxj = static_cast<int>(cellid[j]) - rowbase;
+            const int dcx = (first ? u1 + (cxj - w1) : u2 + (cxj - w2)) - cx;
+            const float rx = (-static_cast<float>(dcx) * wx - sxr) + (xi - ox[j]);
+            const float ry = -static_cast<float>(dy) * wy + (yi - oy[j]);
+            const float rz = -static_cast<float>(dz) * wz + (zi - oz[j]);
+            const float r2 = rx * rx + ry * ry + rz * rz;
+            hit = (r2 < A.rc2) && (r2 > 0.f) && (j != i);
+            if (hit && !A.dpd_on_bonded) {
+              const int lo = min(i, j), hi = max(i, j);
+              if (hi == lo + 1 && hi < sB.n_poly && (hi % A.chain_len) != 0) hit = false;
+            }
+            ent = pack_pair(i, j, dcx, dy, dz, ikm, cross);
+          }
+          const unsigned bal = __ballot_sync(FULL, hit);
+          if (hit) queue[count + __popc(bal & lt_mask)] = ent;
+          count += __popc(bal);
+          if (count >= 32) {
+            __syncwarp();
+            eval_pair(queue[lane]);
+            __syncwarp();
+            if (lane < count - 32) queue[lane] = queue[32 + lane];
+            __syncwarp();
+            count -= 32;
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (lane < count) eval_pair(queue[lane]);
+    __syncthreads();
+    if (A.init_forces) break;
+
+    // ---- D: second half kick, AFBC imposition, IK kinetic part, reduction
+    for (int i = tid; i < N; i += T) {
+      float v0 = vx[i] + A.hdt_m * fx[i];
+      float v1 = vy[i] + A.hdt_m * fy[i];
+      float v2 = vz[i] + A.hdt_m * fz[i];
+      int cx, cy, cz;
+      cell_coords(cellid[i], nx, nxy, inx, inxy, cx, cy, cz);
+      const float rpx = static_cast<float>(cx) * wx + ox[i] - hx;
+      const float rpy = static_cast<float>(cy) * wy + oy[i] - hy;
+      const float rpz = static_cast<float>(cz) * wz + oz[i] - hz;
+      bool sample = true;
+      float u0 = 0.f, u1 = 0.f, u2 = 0.f;
+      if (afbc) {
+        const bool core = fabsf(rpx) < sB.half_core[0] && fabsf(rpy) < sB.half_core[1] &&
+                          fabsf(rpz) < sB.half_core[2];
+        const bool inbc = fabsf(rpx) < sB.half_bc[0] && fabsf(rpy) < sB.half_bc[1] &&
+                          fabsf(rpz) < sB.half_bc[2];
+        u0 = sL[0] * rpx + sL[1] * rpy + sL[2] * rpz;
+        u1 = sL[3] * rpx + sL[4] * rpy + sL[5] * rpz;
+        u2 = sL[6] * rpx + sL[7] * rpy + sL[8] * rpz;
+        if (!core && inbc) {
+          v0 = u0; v1 = u1; v2 = u2;
+        }
+        sample = core;
+      } else if (le) {
+        u0 = gdot * rpy;
+      }
+      vx[i] = v0; vy[i] = v1; vz[i] = v2;
+      if (sample) {
+        const float d0 = v0 - u0, d1 = v1 - u1, d2 = v2 - u2;
+        W[0] += A.mass * d0 * d0;
+        W[1] += A.mass * d1 * d1;
+        W[2] += A.mass * d2 * d2;
+        W[3] += A.mass * d0 * d1;
+        W[4] += A.mass * d0 * d2;
+        W[5] += A.mass * d1 * d2;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const float v = lhmm::warp_sum(W[k]);
+      if (lane == 0) red[6 * warp + k] = v;
+    }
+    __syncthreads();
+    if (tid < 6) {
+      float sum = 0.f;
+      for (int w = 0; w < NW; ++w) sum += red[6 * w + tid];
+      const double pi = -static_cast<double>(sum) * static_cast<double>(sB.inv_vcore);
+      acc_sum += pi;
+      acc_sq += pi * pi;
+    }
+    __syncthreads();
+  }
+
+  // write back
+  for (int i = tid; i < N; i += T) {
+    const float4 v = make_float4(vx[i], vy[i], vz[i], 0.f);
+    const float4 f = make_float4(fx[i], fy[i], fz[i], 0.f);
+    if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(f.x) && isfinite(f.y) &&
+          isfinite(f.z)))
+      status |= LHMM_BOX_NAN;
+    A.pos[off + i] = make_float4(ox[i], oy[i], oz[i], __int_as_float(static_cast<int>(cellid[i])));
+    A.vel[off + i] = v;
+    A.frc[off + i] = f;
+  }
+  if (status) atomicOr(&A.state[bid].status, status);
+  if (!A.init_forces && A.n_steps > 0) {
+    if (tid < 6) {
+      const double inv = 1.0 / static_cast<double>(A.n_steps);
+      A.stress[6 * bid + tid] = A.out_scale * acc_sum * inv;
+      if (A.stress_sq) A.stress_sq[6 * bid + tid] = A.out_scale * A.out_scale * acc_sq * inv;
+    }
+    if (tid == 0) {
+      A.state[bid].step = step0 + static_cast<unsigned long long>(A.n_steps);
+      if (le) {
+        float l = le0 + static_cast<float>(A.n_steps) * le_inc;
+        l -= floorf(l / sB.len[0]) * sB.len[0];
+        if (l >= sB.len[0]) l -= sB.len[0];
+        A.state[bid].le_offset = l;
+      }
+    }
+  }
+}
+
+// Launch variants: threads per block and the resident blocks per SM that
+// the register allocation must allow (64 registers/thread for 2048/SM).
+struct Variant {
+  int threads, min_blocks;
+};
+constexpr Variant kVariants[] = {{256, 4}, {512, 2}, {1024, 1}, {256, 2}, {512, 1}};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+template <int T, int MINB>
+cudaError_t launch_micro(const MicroArgs& a, int grid, size_t smem, cudaStream_t s) {
+  static size_t attr_bytes = 0;
+  if (smem > attr_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(micro_kernel<T, MINB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    attr_bytes = smem;
+  }
+  micro_kernel<T, MINB><<<grid, T, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_variant(int v, const MicroArgs& a, int grid, size_t smem, cudaStream_t s) {
+  if (grid <= 0) return cudaSuccess;
+  switch (v) {
+    case 0: return launch_micro<256, 4>(a, grid, smem, s);
+    case 1: return launch_micro<512, 2>(a, grid, smem, s);
+    case 2: return launch_micro<1024, 1>(a, grid, smem, s);
+    case 3: return launch_micro<256, 2>(a, grid, smem, s);
+    default: return launch_micro<512, 1>(a, grid, smem, s);
+  }
+}
+
+// A size class: boxes of similar bead count launched together with a shared
+// memory plan sized to the class, on a stream of its own.
+struct SizeClass {
+  std::vector<int> boxes;  // host copy, longest first
+  int* boxes_d = nullptr;
+  int max_beads = 1, max_cells = 1;
+  int variant = 1;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+};
+
+}  // namespace
+
+struct lhmm_micro_s {
+  lhmm_dpd_params p;
+  int n_boxes = 0, chain_len = 0, max_beads = 0, max_cells = 0;
+  long long total = 0;
+  std::vector<BoxInfo> info;
+  BoxInfo* info_d = nullptr;
+  BoxState* state_d = nullptr;
+  float4 *pos_d = nullptr, *vel_d = nullptr, *frc_d = nullptr;
+  int* order_d = nullptr;
+  float* L_stage = nullptr;
+  double *st_stage = nullptr, *sq_stage = nullptr;
+  cudaStream_t stream = nullptr;
+  std::vector<SizeClass> classes;
+  cudaEvent_t fork = nullptr;
+  int subset_variant = 1;  // single launch over a device-side box list
+};
+
+namespace {
+
+size_t max_optin_smem() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return static_cast<size_t>(v);
+}
+
+size_t class_smem(int max_beads, int max_cells, int variant) {
+  return micro_smem_bytes(max_beads, max_cells, kVariants[variant].threads);
+}
+
+// heuristic start: more threads for larger boxes; the autotuner refines it
+int default_variant(int n) { return n <= 1100 ? 0 : (n <= 2600 ? 1 : 2); }
+
+void abs_to_rel(const BoxInfo& B, const double* x, float4* out, int n) {
+  for (int i = 0; i < n; ++i) {
+    int c[3];
+    float o[3];
+    for (int a = 0; a < 3; ++a) {
+      const double len = B.len[a], w = B.w[a];
+      double xa = x[3 * i + a];
+      xa -= std::floor(xa / len) * len;
+      if (xa >= len) xa -= len;
+      if (xa < 0.0) xa = 0.0;
+      int ca = static_cast<int>(std::floor(xa / w));
+      ca = std::min(std::max(ca, 0), B.nc[a] - 1);
+      double oa = xa - static_cast<double>(ca) * w;  // exact for x = c w + o
+      if (oa < 0.0) oa = 0.0;
+      if (oa > w) oa = w;
+      c[a] = ca;
+      o[a] = static_cast<float>(oa);
+    }
+    const int cell = c[0] + B.nc[0] * (c[1] + B.nc[1] * c[2]);
+    float cw;
+    std::memcpy(&cw, &cell, sizeof(float));
+    out[i] = make_float4(o[0], o[1], o[2], cw);
+  }
+}
+
+void rel_to_abs(const BoxInfo& B, const float4* in, double* x, int n) {
+  for (int i = 0; i < n; ++i) {
+    int cell;
+    std::memcpy(&cell, &in[i].w, sizeof(int));
+    const int c[3] = {cell % B.nc[0], (cell / B.nc[0]) % B.nc[1], cell / (B.nc[0] * B.nc[1])};
+    const float o[3] = {in[i].x, in[i].y, in[i].z};
+    for (int a = 0; a < 3; ++a)
+      x[3 * i + a] = static_cast<double>(c[a]) * static_cast<double>(B.w[a]) + static_cast<double>(o[a]);
+  }
+}
+
+void free_micro(lhmm_micro_t h) {
+  if (!h) return;
+  cudaFree(h->info_d);
+  cudaFree(h->state_d);
+  cudaFree(h->pos_d);
+  cudaFree(h->vel_d);
+  cudaFree(h->frc_d);
+  cudaFree(h->order_d);
+  cudaFree(h->L_stage);
+  cudaFree(h->st_stage);
+  cudaFree(h->sq_stage);
+  for (auto& c : h->classes) {
+    cudaFree(c.boxes_d);
+    if (c.stream) cudaStreamDestroy(c.stream);
+    if (c.done) cudaEventDestroy(c.done);
+  }
+  if (h->fork) cudaEventDestroy(h->fork);
+  delete h;
+}
+
+MicroArgs make_args(const lhmm_micro_s* h) {
+  MicroArgs a{};
+  const lhmm_dpd_params& p = h->p;
+  a.boxes = h->info_d;
+  a.state = h->state_d;
+  a.pos = h->pos_d;
+  a.vel = h->vel_d;
+  a.frc = h->frc_d;
+  a.a = p.a_ij;
+  a.gamma = p.gamma;
+  a.sig_dt = static_cast<float>(static_cast<double>(p.sigma) / std::sqrt(static_cast<double>(p.dt)));
+  a.rc = p.rc;
+  a.rc2 = p.rc * p.rc;
+  a.rcinv = static_cast<float>(1.0 / static_cast<double>(p.rc));
+  a.H = p.H_fene;
+  a.R0 = p.R0;
+  a.inv_R0sq = static_cast<float>(1.0 / (static_cast<double>(p.R0) * p.R0));
+  a.dt = p.dt;
+  a.hdt_m = static_cast<float>(0.5 * static_cast<double>(p.dt) / p.mass);
+  a.mass = p.mass;
+  a.lambda_star = static_cast<float>(p.lambda_star);
+  a.out_scale = p.alpha / p.lambda_star;
+  a.seed_lo = static_cast<unsigned>(p.seed & 0xffffffffu);
+  a.seed_hi = static_cast<unsigned>(p.seed >> 32);
+  a.flow = p.flow_mode;
+  a.dpd_on_bonded = p.dpd_on_bonded;
+  a.chain_len = h->chain_len > 0 ? h->chain_len : 1;
+  a.max_beads = h->max_beads;
+  a.max_cells = h->max_cells;
+  a.n_boxes = h->n_boxes;
+  return a;
+}
+
+// Launch every size class on its own stream, forked from and joined back
+// into `s` with events (capturable into a CUDA graph).
+cudaError_t launch_classes(lhmm_micro_s* h, MicroArgs a, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = cudaEventRecord(h->fork, s)) != cudaSuccess) return e;
+  for (auto& c : h->classes) {
+    if ((e = cudaStreamWaitEvent(c.stream, h->fork, 0)) != cudaSuccess) return e;
+    a.list = c.boxes_d;
+    a.max_beads = c.max_beads;
+    a.max_cells = c.max_cells;
+    if ((e = launch_variant(c.variant, a, static_cast<int>(c.boxes.size()),
+                            class_smem(c.max_beads, c.max_cells, c.variant), c.stream)) != cudaSuccess)
+      return e;
+    if ((e = cudaEventRecord(c.done, c.stream)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(s, c.done, 0)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_subset(lhmm_micro_s* h, MicroArgs a, const int* list, int n, cudaStream_t s) {
+  a.list = list;
+  a.max_beads = h->max_beads;
+  a.max_cells = h->max_cells;
+  return launch_variant(h->subset_variant, a, n,
+                        class_smem(h->max_beads, h->max_cells, h->subset_variant), s);
+}
+
+}  // namespace
+
+extern "C" lhmm_status lhmm_micro_create(const lhmm_dpd_params* params,
+                                         const lhmm_batch_desc* batch, const double* pos0_host,
+                                         const float* vel0_host, const float* L0_host,
+                                         void* stream, lhmm_micro_t* out) {
+  if (!params || !batch || !out || batch->n_boxes < 0) return LHMM_ERR_ARG;
+  *out = nullptr;
+  const lhmm_dpd_params& p = *params;
+  if (!(p.rc > 0.f) || !(p.dt > 0.f) || !(p.mass > 0.f) || !(p.R0 > 0.f) ||
+      !(p.lambda_star != 0.0) || p.flow_mode < 0 || p.flow_mode > 2)
+    return LHMM_ERR_ARG;
+  const int nb = batch->n_boxes;
+  if (nb > 0 && (!batch->box_edge || !batch->n_beads || !batch->n_chains)) return LHMM_ERR_ARG;
+  std::vector<BoxInfo> info(nb);
+  long long total = 0;
+  int max_beads = 1, max_cells = 1;
+  for (int b = 0; b < nb; ++b) {
+    BoxInfo& B = info[b];
+    const int n = batch->n_beads[b], nch = batch->n_chains[b];
+    if (n < 0 || n > 65535 || nch < 0) return LHMM_ERR_ARG;
+    if (nch > 0 && (batch->chain_len < 2 || (long long)nch * batch->chain_len > n))
+      return LHMM_ERR_ARG;
+    B.off = total;
+    B.n = n;
+    B.n_poly = nch * (nch > 0 ? batch->chain_len : 0);
+    long long ncell = 1;
+    float vol = 1.f;
+    for (int a = 0; a < 3; ++a) {
+      const float E = batch->box_edge[3 * b + a];
+      if (!(E >= 3.f * p.rc)) return LHMM_ERR_ARG;
+      B.nc[a] = static_cast<int>(std::floor(E / p.rc));
+      B.w[a] = E / static_cast<float>(B.nc[a]);
+      B.winv[a] = 1.f / B.w[a];
+      B.len[a] = static_cast<float>(B.nc[a]) * B.w[a];
+      B.half_core[a] = 0.5f * p.afbc_core_frac * B.len[a];
+      B.half_bc[a] = (0.5f * p.afbc_core_frac + p.afbc_bc_frac) * B.len[a];
+      ncell *= B.nc[a];
+      vol *= (p.flow_mode == LHMM_FLOW_AFBC) ? p.afbc_core_frac * B.len[a] : B.len[a];
+    }
+    if (ncell > 65535) return LHMM_ERR_UNSUPPORTED;
+    // Lees-Edwards rows store the x cell offset of a sliding image in 8 bits
+    if (p.flow_mode == LHMM_FLOW_LEES_EDWARDS && B.nc[0] > 60) return LHMM_ERR_UNSUPPORTED;
+    B.ncell = static_cast<int>(ncell);
+    B.inv_vcore = 1.f / vol;
+    total += n;
+    max_beads = std::max(max_beads, n);
+    max_cells = std::max(max_cells, B.ncell);
+  }
+  if (total > 0 && (!pos0_host || !vel0_host)) return LHMM_ERR_ARG;
+  // queue entries hold 16-bit bead ids; the whole box must fit in shared memory
+  if (max_beads > 8191) return LHMM_ERR_UNSUPPORTED;
+  const size_t optin = max_optin_smem();
+  lhmm_micro_s* h = new lhmm_micro_s();
+  h->p = p;
+  h->n_boxes = nb;
+  h->chain_len = batch->chain_len;
+  h->max_beads = max_beads;
+  h->max_cells = max_cells;
+  h->total = total;
+  h->info = info;
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->subset_variant = default_variant(max_beads);
+  auto fail = [&](lhmm_status s) {
+    free_micro(h);
+    return s;
+  };
+  if (class_smem(max_beads, max_cells, h->subset_variant) > optin) {
+    h->subset_variant = 0;  // fewer warps, smaller queues
+    if (class_smem(max_beads, max_cells, 0) > optin) return fail(LHMM_ERR_UNSUPPORTED);
+  }
+  // size classes: one per distinct bead count, merged down to at most 12
+  std::vector<int> order(nb);
+  for (int b = 0; b < nb; ++b) order[b] = b;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return info[x].n > info[y].n; });  // longest first
+  {
+    std::vector<std::vector<int>> groups;
+    for (int b : order) {
+      if (groups.empty() || info[groups.back().front()].n != info[b].n) groups.push_back({});
+      groups.back().push_back(b);
+    }
+    while (groups.size() > 12) {  // merge the two smallest adjacent groups
+      size_t best = 0;
+      for (size_t g = 1; g + 1 < groups.size(); ++g)
+        if (groups[g].size() + groups[g + 1].size() <
+            groups[best].size() + groups[best + 1].size())
+          best = g;
+      groups[best].insert(groups[best].end(), groups[best + 1].begin(), groups[best + 1].end());
+      groups.erase(groups.begin() + best + 1);
+    }
+    for (auto& g : groups) {
+      SizeClass c;
+      c.boxes = g;
+      for (int b : g) {
+        c.max_beads = std::max(c.max_beads, info[b].n);
+        c.max_cells = std::max(c.max_cells, info[b].ncell);
+      }
+      c.variant = default_variant(c.max_beads);
+      if (class_smem(c.max_beads, c.max_cells, c.variant) > optin) c.variant = 0;
+      h->classes.push_back(std::move(c));
+    }
+  }
+  const size_t nbx = static_cast<size_t>(std::max(nb, 1));
+  const size_t nbead = static_cast<size_t>(std::max(total, 1LL));
+  cudaError_t e = cudaSuccess;
+  if ((e = cudaMalloc(&h->info_d, sizeof(BoxInfo) * nbx)) != cudaSuccess ||
+      (e = cudaMalloc(&h->state_d, sizeof(BoxState) * nbx)) != cudaSuccess ||
+      (e = cudaMalloc(&h->pos_d, sizeof(float4) * nbead)) != cudaSuccess ||
+      (e = cudaMalloc(&h->vel_d, sizeof(float4) * nbead)) != cudaSuccess ||
+      (e = cudaMalloc(&h->frc_d, sizeof(float4) * nbead)) != cudaSuccess ||
+      (e = cudaMalloc(&h->order_d, sizeof(int) * nbx)) != cudaSuccess ||
+      (e = cudaMalloc(&h->L_stage, sizeof(float) * 9 * nbx)) != cudaSuccess ||
+      (e = cudaMalloc(&h->st_stage, sizeof(double) * 6 * nbx)) != cudaSuccess ||
+      (e = cudaMalloc(&h->sq_stage, sizeof(double) * 6 * nbx)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming)) != cudaSuccess)
+    return fail(lhmm_cuda_error(e));
+  for (auto& c : h->classes) {
+    if ((e = cudaMalloc(&c.boxes_d, sizeof(int) * c.boxes.size())) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaMemcpy(c.boxes_d, c.boxes.data(), sizeof(int) * c.boxes.size(),
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+      return fail(lhmm_cuda_error(e));
+  }
+  // host-side conversion of the initial state to cell-relative form
+  std::vector<float4> pos(nbead), vel(nbead), zero(nbead, make_float4(0.f, 0.f, 0.f, 0.f));
+  for (int b = 0; b < nb; ++b) {
+    const BoxInfo& B = info[b];
+    abs_to_rel(B, pos0_host + 3 * B.off, pos.data() + B.off, B.n);
+    for (int i = 0; i < B.n; ++i) {
+      const float* v = vel0_host + 3 * (B.off + i);
+      vel[B.off + i] = make_float4(v[0], v[1], v[2], 0.f);
+    }
+  }
+  std::vector<BoxState> st(nbx);
+  for (auto& x : st) x = BoxState{0ull, 0.f, 0u};
+  cudaStream_t s = h->stream;
+  if ((e = cudaMemcpyAsync(h->info_d, info.data(), sizeof(BoxInfo) * nb, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h->state_d, st.data(), sizeof(BoxState) * nbx, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h->pos_d, pos.data(), sizeof(float4) * total, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h->vel_d, vel.data(), sizeof(float4) * total, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h->frc_d, zero.data(), sizeof(float4) * total, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h->order_d, order.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(h->L_stage, 0, sizeof(float) * 9 * nbx, s)) != cudaSuccess)
+    return fail(lhmm_cuda_error(e));
+  if (L0_host && nb > 0 &&
+      (e = cudaMemcpyAsync(h->L_stage, L0_host, sizeof(float) * 9 * nb, cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess)
+    return fail(lhmm_cuda_error(e));
+  // initial forces F(0) from (r0, v0) with the step-0 random stream
+  MicroArgs a = make_args(h);
+  a.L = h->L_stage;
+  a.init_forces = 1;
+  a.n_steps = 0;
+  if ((e = launch_subset(h, a, h->order_d, nb, s)) != cudaSuccess) return fail(lhmm_cuda_error(e));
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(lhmm_cuda_error(e));
+  *out = h;
+  return LHMM_OK;
+}
+
+extern "C" lhmm_status lhmm_micro_destroy(lhmm_micro_t h) {
+  if (!h) return LHMM_ERR_ARG;
+  cudaStreamSynchronize(h->stream);
+  cudaDeviceSynchronize();
+  free_micro(h);
+  return LHMM_OK;
+}
+
+extern "C" lhmm_status lhmm_micro_advance(lhmm_micro_t h, const float* L_dev,
+                                          const int* box_idx_dev, int n_active, int n_steps,
+                                          double* stress_dev, double* stress_sq_dev,
+                                          void* stream) {
+  if (!h || n_steps < 0 || n_active < 0) return LHMM_ERR_ARG;
+  if (box_idx_dev == nullptr && n_active != h->n_boxes) return LHMM_ERR_ARG;
+  if (box_idx_dev != nullptr && n_active > h->n_boxes) return LHMM_ERR_ARG;
+  if (n_steps == 0 || n_active == 0) return LHMM_OK;
+  if (!L_dev || !stress_dev) return LHMM_ERR_ARG;
+  MicroArgs a = make_args(h);
+  a.L = L_dev;
+  a.stress = stress_dev;
+  a.stress_sq = stress_sq_dev;
+  a.n_steps = n_steps;
+  a.init_forces = 0;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (box_idx_dev) {
+    LHMM_CK(launch_subset(h, a, box_idx_dev, n_active, s));
+  } else {
+    LHMM_CK(launch_classes(h, a, s));
+  }
+  return LHMM_OK;
+}
+
+extern "C" lhmm_status lhmm_micro_advance_host(lhmm_micro_t h, const float* L_host, int n_steps,
+                                               double* stress_host, double* stress_sq_host,
+                                               void* stream) {
+  if (!h || !L_host || !stress_host || n_steps < 0) return LHMM_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t nb = static_cast<size_t>(h->n_boxes);
+  LHMM_CK(cudaMemcpyAsync(h->L_stage, L_host, sizeof(float) * 9 * nb, cudaMemcpyHostToDevice, s));
+  lhmm_status st = lhmm_micro_advance(h, h->L_stage, nullptr, h->n_boxes, n_steps, h->st_stage,
+                                      stress_sq_host ? h->sq_stage : nullptr, stream);
+  if (st != LHMM_OK) return st;
+  LHMM_CK(cudaMemcpyAsync(stress_host, h->st_stage, sizeof(double) * 6 * nb, cudaMemcpyDeviceToHost, s));
+  if (stress_sq_host)
+    LHMM_CK(cudaMemcpyAsync(stress_sq_host, h->sq_stage, sizeof(double) * 6 * nb,
+                            cudaMemcpyDeviceToHost, s));
+  LHMM_CK(cudaStreamSynchronize(s));
+  return LHMM_OK;
+}
+
+extern "C" lhmm_status lhmm_micro_sync(lhmm_micro_t h, uint32_t* box_status_host) {
+  if (!h) return LHMM_ERR_ARG;
+  LHMM_CK(cudaDeviceSynchronize());
+  std::vector<BoxState> st(static_cast<size_t>(std::max(h->n_boxes, 1)));
+  LHMM_CK(cudaMemcpy(st.data(), h->state_d, sizeof(BoxState) * h->n_boxes, cudaMemcpyDeviceToHost));
+  unsigned all = 0;
+  for (int b = 0; b < h->n_boxes; ++b) {
+    if (box_status_host) box_status_host[b] = st[b].status;
+    all |= st[b].status;
+    st[b].status = 0;
+  }
+  if (all) LHMM_CK(cudaMemcpy(h->state_d, st.data(), sizeof(BoxState) * h->n_boxes, cudaMemcpyHostToDevice));
+  if (all & LHMM_BOX_BOND_OVERSTRETCH) return LHMM_ERR_BOND_OVERSTRETCH;
+  if (all & LHMM_BOX_NAN) return LHMM_ERR_NAN;
+  if (all & LHMM_BOX_CELL_OVERFLOW) return LHMM_ERR_CELL_OVERFLOW;
+  return LHMM_OK;
+}
+
+extern "C" lhmm_status lhmm_micro_get_state(lhmm_micro_t h, int box, double* pos_host,
+                                            float* vel_host, float* force_host, uint64_t* step,
+                                            float* le_offset) {
+  if (!h || box < 0 || box >= h->n_boxes) return LHMM_ERR_ARG;
+  LHMM_CK(cudaStreamSynchronize(h->stream));
+  LHMM_CK(cudaDeviceSynchronize());
+  const BoxInfo& B = h->info[box];
+  std::vector<float4> buf(static_cast<size_t>(std::max(B.n, 1)));
+  if (pos_host && B.n) {
+    LHMM_CK(cudaMemcpy(buf.data(), h->pos_d + B.off, sizeof(float4) * B.n, cudaMemcpyDeviceToHost));
+    rel_to_abs(B, buf.data(), pos_host, B.n);
+  }
+  float* outs[2] = {vel_host, force_host};
+  float4* srcs[2] = {h->vel_d, h->frc_d};
+  for (int k = 0; k < 2; ++k) {
+    if (!outs[k] || !B.n) continue;
+    LHMM_CK(cudaMemcpy(buf.data(), srcs[k] + B.off, sizeof(float4) * B.n, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < B.n; ++i) {
+      outs[k][3 * i] = buf[i].x;
+      outs[k][3 * i + 1] = buf[i].y;
+      outs[k][3 * i + 2] = buf[i].z;
+    }
+  }
+  if (step || le_offset) {
+    BoxState s;
+    LHMM_CK(cudaMemcpy(&s, h->state_d + box, sizeof(BoxState), cudaMemcpyDeviceToHost));
+    if (step) *step = s.step;
+    if (le_offset) *le_offset = s.le_offset;
+  }
+  return LHMM_OK;
+}
+
+extern "C" lhmm_status lhmm_micro_set_state(lhmm_micro_t h, int box, const double* pos_host,
+                                            const float* vel_host, const float* force_host,
+                                            uint64_t step, float le_offset) {
+  if (!h || box < 0 || box >= h->n_boxes || !pos_host || !vel_host || !force_host)
+    return LHMM_ERR_ARG;
+  LHMM_CK(cudaDeviceSynchronize());
+  const BoxInfo& B = h->info[box];
+  if (B.n) {
+    std::vector<float4> buf(static_cast<size_t>(B.n));
+    abs_to_rel(B, pos_host, buf.data(), B.n);
+    LHMM_CK(cudaMemcpy(h->pos_d + B.off, buf.data(), sizeof(float4) * B.n, cudaMemcpyHostToDevice));
+    for (int i = 0; i < B.n; ++i)
+      buf[i] = make_float4(vel_host[3 * i], vel_host[3 * i + 1], vel_host[3 * i + 2], 0.f);
+    LHMM_CK(cudaMemcpy(h->vel_d + B.off, buf.data(), sizeof(float4) * B.n, cudaMemcpyHostToDevice));
+    for (int i = 0; i < B.n; ++i)
+      buf[i] = make_float4(force_host[3 * i], force_host[3 * i + 1], force_host[3 * i + 2], 0.f);
+    LHMM_CK(cudaMemcpy(h->frc_d + B.off, buf.data(), sizeof(float4) * B.n, cudaMemcpyHostToDevice));
+  }
+  BoxState s{step, le_offset, 0u};
+  LHMM_CK(cudaMemcpy(h->state_d + box, &s, sizeof(BoxState), cudaMemcpyHostToDevice));
+  return LHMM_OK;
+}
+
+extern "C" lhmm_status lhmm_micro_info(lhmm_micro_t h, int* n_boxes, int64_t* total_beads,
+                                       int* max_beads) {
+  if (!h) return LHMM_ERR_ARG;
+  if (n_boxes) *n_boxes = h->n_boxes;
+  if (total_beads) *total_beads = h->total;
+  if (max_beads) *max_beads = h->max_beads;
+  return LHMM_OK;
+}
+
+namespace {
+// process-wide autotune cache: (largest box, cells, flow, device) -> variant
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, int> g_tune_cache;
+}  // namespace
+
+extern "C" lhmm_status lhmm_micro_autotune(lhmm_micro_t h, const float* L_dev, int probe_steps,
+                                           void* stream) {
+  if (!h || !L_dev || probe_steps < 1) return LHMM_ERR_ARG;
+  if (h->total == 0) return LHMM_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  LHMM_CK(cudaGetDevice(&dev));
+  LHMM_CK(cudaStreamSynchronize(s));
+  LHMM_CK(cudaDeviceSynchronize());
+  const size_t nb = static_cast<size_t>(h->n_boxes), nt = static_cast<size_t>(h->total);
+  float4 *sp = nullptr, *sv = nullptr, *sf = nullptr;
+  BoxState* ss = nullptr;
+  cudaError_t e;
+  auto cleanup = [&]() {
+    cudaFree(sp);
+    cudaFree(sv);
+    cudaFree(sf);
+    cudaFree(ss);
+  };
+  if ((e = cudaMalloc(&sp, sizeof(float4) * nt)) != cudaSuccess ||
+      (e = cudaMalloc(&sv, sizeof(float4) * nt)) != cudaSuccess ||
+      (e = cudaMalloc(&sf, sizeof(float4) * nt)) != cudaSuccess ||
+      (e = cudaMalloc(&ss, sizeof(BoxState) * nb)) != cudaSuccess ||
+      (e = cudaMemcpy(sp, h->pos_d, sizeof(float4) * nt, cudaMemcpyDeviceToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(sv, h->vel_d, sizeof(float4) * nt, cudaMemcpyDeviceToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(sf, h->frc_d, sizeof(float4) * nt, cudaMemcpyDeviceToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(ss, h->state_d, sizeof(BoxState) * nb, cudaMemcpyDeviceToDevice)) != cudaSuccess) {
+    cleanup();
+    return lhmm_cuda_error(e);
+  }
+  const size_t optin = max_optin_smem();
+  MicroArgs a = make_args(h);
+  a.L = L_dev;
+  a.stress = h->st_stage;
+  a.stress_sq = nullptr;
+  a.n_steps = probe_steps;
+  a.init_forces = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  lhmm_status result = LHMM_OK;
+  for (auto& c : h->classes) {
+    const auto key = std::make_tuple(c.max_beads, c.max_cells, h->p.flow_mode, dev);
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) {
+        c.variant = it->second;
+        continue;
+      }
+    }
+    a.list = c.boxes_d;
+    a.max_beads = c.max_beads;
+    a.max_cells = c.max_cells;
+    float best = 1e30f;
+    int best_v = c.variant;
+    for (int v = 0; v < kNumVariants; ++v) {
+      const size_t sm = class_smem(c.max_beads, c.max_cells, v);
+      if (sm > optin) continue;
+      const int grid = static_cast<int>(c.boxes.size());
+      float ms = 0.f;
+      if ((e = launch_variant(v, a, grid, sm, s)) != cudaSuccess ||  // warm-up
+          (e = cudaEventRecord(e0, s)) != cudaSuccess ||
+          (e = launch_variant(v, a, grid, sm, s)) != cudaSuccess ||
+          (e = cudaEventRecord(e1, s)) != cudaSuccess ||
+          (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+          (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) {
+        result = lhmm_cuda_error(e);
+        break;
+      }
+      if (ms < best) {
+        best = ms;
+        best_v = v;
+      }
+    }
+    if (result != LHMM_OK) break;
+    c.variant = best_v;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best_v;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // restore the state the probes advanced
+  if ((e = cudaMemcpy(h->pos_d, sp, sizeof(float4) * nt, cudaMemcpyDeviceToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(h->vel_d, sv, sizeof(float4) * nt, cudaMemcpyDeviceToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(h->frc_d, sf, sizeof(float4) * nt, cudaMemcpyDeviceToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(h->state_d, ss, sizeof(BoxState) * nb, cudaMemcpyDeviceToDevice)) != cudaSuccess) {
+    cleanup();
+    return lhmm_cuda_error(e);
+  }
+  cleanup();
+  return result;
+}
+
+extern "C" lhmm_status lhmm_micro_plan(lhmm_micro_t h, int* n_classes, int cap, int* class_boxes,
+                                       int* class_max_beads, int* class_threads,
+                                       int* class_min_blocks) {
+  if (!h || !n_classes) return LHMM_ERR_ARG;
+  *n_classes = static_cast<int>(h->classes.size());
+  for (int k = 0; k < cap && k < *n_classes; ++k) {
+    const SizeClass& c = h->classes[k];
+    if (class_boxes) class_boxes[k] = static_cast<int>(c.boxes.size());
+    if (class_max_beads) class_max_beads[k] = c.max_beads;
+    if (class_threads) class_threads[k] = kVariants[c.variant].threads;
+    if (class_min_blocks) class_min_blocks[k] = kVariants[c.variant].min_blocks;
+  }
+  return LHMM_OK;
+}
+
+extern "C" lhmm_status lhmm_micro_set_variant(lhmm_micro_t h, int cls, int variant) {
+  if (!h || variant < 0 || variant >= kNumVariants) return LHMM_ERR_ARG;
+  if (cls < 0 || cls >= static_cast<int>(h->classes.size())) return LHMM_ERR_ARG;
+  SizeClass& c = h->classes[cls];
+  if (class_smem(c.max_beads, c.max_cells, variant) > max_optin_smem()) return LHMM_ERR_UNSUPPORTED;
+  c.variant = variant;
+  return LHMM_OK;
+}

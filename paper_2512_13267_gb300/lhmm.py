@@ -1,0 +1,235 @@
+"""Thin ctypes binding of the LHMM C ABI (include/lhmm.h).
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+library.  Device buffers are torch CUDA tensors (their data_ptr is passed),
+streams are torch.cuda.Stream objects or raw cudaStream_t integers.  If the
+library is missing this module raises; there is no CPU fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblhmm.so")
+
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_BOND_OVERSTRETCH, ERR_CELL_OVERFLOW, ERR_NAN, \
+    ERR_TIMEOUT, ERR_UNSUPPORTED = range(9)
+BOX_BOND_OVERSTRETCH, BOX_NAN, BOX_CELL_OVERFLOW = 1, 2, 4
+FLOW_PERIODIC, FLOW_LEES_EDWARDS, FLOW_AFBC = 0, 1, 2
+FLOWS = {"periodic": FLOW_PERIODIC, "lees_edwards": FLOW_LEES_EDWARDS, "afbc": FLOW_AFBC}
+
+
+class LhmmError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} (status {status})")
+
+
+class DpdParams(C.Structure):
+    _fields_ = [
+        ("a_ij", C.c_float), ("gamma", C.c_float), ("sigma", C.c_float), ("kBT", C.c_float),
+        ("rc", C.c_float), ("H_fene", C.c_float), ("R0", C.c_float), ("dt", C.c_float),
+        ("mass", C.c_float), ("seed", C.c_uint64), ("flow_mode", C.c_int),
+        ("afbc_core_frac", C.c_float), ("afbc_bc_frac", C.c_float), ("dpd_on_bonded", C.c_int),
+        ("alpha", C.c_double), ("lambda_star", C.c_double),
+    ]
+
+
+class BatchDesc(C.Structure):
+    _fields_ = [("n_boxes", C.c_int), ("box_edge", C.POINTER(C.c_float)),
+                ("n_beads", C.POINTER(C.c_int)), ("n_chains", C.POINTER(C.c_int)),
+                ("chain_len", C.c_int)]
+
+
+_lib = None
+_F = C.POINTER(C.c_float)
+_D = C.POINTER(C.c_double)
+_I = C.POINTER(C.c_int)
+_U32 = C.POINTER(C.c_uint32)
+_U64 = C.POINTER(C.c_uint64)
+
+
+def lib():
+    """Load liblhmm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+        L = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        L.lhmm_status_string.argtypes = [C.c_int]
+        L.lhmm_status_string.restype = C.c_char_p
+        L.lhmm_micro_create.argtypes = [C.POINTER(DpdParams), C.POINTER(BatchDesc), _D, _F, _F,
+                                        vp, C.POINTER(vp)]
+        L.lhmm_micro_destroy.argtypes = [vp]
+        L.lhmm_micro_advance.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp, vp, vp]
+        L.lhmm_micro_advance_host.argtypes = [vp, _F, C.c_int, _D, _D, vp]
+        L.lhmm_micro_sync.argtypes = [vp, _U32]
+        L.lhmm_micro_get_state.argtypes = [vp, C.c_int, _D, _F, _F, _U64, _F]
+        L.lhmm_micro_set_state.argtypes = [vp, C.c_int, _D, _F, _F, C.c_uint64, C.c_float]
+        L.lhmm_micro_info.argtypes = [vp, _I, C.POINTER(C.c_int64), _I]
+        L.lhmm_micro_autotune.argtypes = [vp, vp, C.c_int, vp]
+        L.lhmm_micro_plan.argtypes = [vp, _I, C.c_int, _I, _I, _I, _I]
+        L.lhmm_micro_set_variant.argtypes = [vp, C.c_int, C.c_int]
+        _lib = L
+    return _lib
+
+
+def status_string(s):
+    return lib().lhmm_status_string(int(s)).decode()
+
+
+def check(status, where):
+    if status != OK:
+        raise LhmmError(status, where)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            return C.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _ptr(t):
+    """Device pointer of a torch CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _np(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(C.POINTER(np.ctypeslib.as_ctypes_type(dtype)))
+
+
+def dpd_params(flow="afbc", seed=1, alpha=1.0, lambda_star=1.0, dpd_on_bonded=1,
+               afbc_core_frac=24.0 / 76.0, afbc_bc_frac=13.0 / 76.0, **phys):
+    d = dict(a_ij=25.0, gamma=4.5, sigma=3.0, kBT=1.0, rc=1.0, H_fene=30.0, R0=1.5, dt=0.01,
+             mass=1.0)
+    d.update(phys)
+    flow_mode = FLOWS[flow] if isinstance(flow, str) else int(flow)
+    return DpdParams(seed=seed, flow_mode=flow_mode, afbc_core_frac=afbc_core_frac,
+                     afbc_bc_frac=afbc_bc_frac, dpd_on_bonded=dpd_on_bonded, alpha=alpha,
+                     lambda_star=lambda_star, **d)
+
+
+class Micro:
+    """A batch of DPD/FENE micro-domains resident on the GPU (lhmm_micro_*)."""
+
+    def __init__(self, params, edges, n_beads, n_chains, chain_len, pos0, vel0, L0=None,
+                 stream=None):
+        L = lib()
+        edges, pe = _np(np.asarray(edges, np.float32).reshape(-1, 3), np.float32)
+        nb, pn = _np(n_beads, np.int32)
+        nch, pc = _np(n_chains, np.int32)
+        pos0, pp = _np(np.asarray(pos0, np.float64).reshape(-1, 3), np.float64)
+        vel0, pv = _np(np.asarray(vel0, np.float32).reshape(-1, 3), np.float32)
+        self.params = params
+        self.n_boxes = int(nb.shape[0])
+        self.n_beads = nb.copy()
+        self.offsets = np.concatenate([[0], np.cumsum(nb.astype(np.int64))])
+        pL = None
+        if L0 is not None:
+            L0, pL = _np(np.asarray(L0, np.float32).reshape(self.n_boxes, 9), np.float32)
+        desc = BatchDesc(self.n_boxes, pe, pn, pc, int(chain_len))
+        h = C.c_void_p()
+        check(L.lhmm_micro_create(C.byref(params), C.byref(desc), pp, pv, pL, _stream_ptr(stream),
+                                  C.byref(h)), "lhmm_micro_create")
+        self.h = h
+
+    @classmethod
+    def from_batch(cls, params, batch, stream=None):
+        return cls(params, batch.edges, batch.n_beads, batch.n_chains, batch.chain_len,
+                   batch.pos, batch.vel, L0=batch.L, stream=stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lhmm_micro_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def advance(self, L_dev, n_steps, stress_dev, stress_sq_dev=None, box_idx_dev=None,
+                stream=None):
+        n_active = self.n_boxes if box_idx_dev is None else int(box_idx_dev.numel())
+        if box_idx_dev is not None and n_active == 0:
+            return  # nothing to advance
+        check(lib().lhmm_micro_advance(self.h, _ptr(L_dev), _ptr(box_idx_dev), n_active,
+                                       int(n_steps), _ptr(stress_dev), _ptr(stress_sq_dev),
+                                       _stream_ptr(stream)), "lhmm_micro_advance")
+
+    def advance_host(self, L_host, n_steps, stress_host=None, stress_sq_host=None, stream=None):
+        L_host, pL = _np(np.asarray(L_host, np.float32).reshape(self.n_boxes, 9), np.float32)
+        if stress_host is None:
+            stress_host = np.zeros((self.n_boxes, 6))
+        ps = stress_host.ctypes.data_as(_D)
+        pq = None if stress_sq_host is None else stress_sq_host.ctypes.data_as(_D)
+        check(lib().lhmm_micro_advance_host(self.h, pL, int(n_steps), ps, pq,
+                                            _stream_ptr(stream)), "lhmm_micro_advance_host")
+        return stress_host
+
+    def sync(self, raise_on_error=True):
+        st = np.zeros(max(self.n_boxes, 1), np.uint32)
+        s = lib().lhmm_micro_sync(self.h, st.ctypes.data_as(_U32))
+        if raise_on_error:
+            check(s, "lhmm_micro_sync")
+        return s, st[: self.n_boxes]
+
+    def get_state(self, box):
+        n = int(self.n_beads[box])
+        pos = np.zeros((n, 3), np.float64)
+        vel = np.zeros((n, 3), np.float32)
+        frc = np.zeros((n, 3), np.float32)
+        step = C.c_uint64()
+        le = C.c_float()
+        check(lib().lhmm_micro_get_state(self.h, int(box), pos.ctypes.data_as(_D),
+                                         vel.ctypes.data_as(_F), frc.ctypes.data_as(_F),
+                                         C.byref(step), C.byref(le)), "lhmm_micro_get_state")
+        return pos, vel, frc, int(step.value), float(le.value)
+
+    def set_state(self, box, pos, vel, force, step, le_offset=0.0):
+        pos, pp = _np(np.asarray(pos, np.float64).reshape(-1, 3), np.float64)
+        vel, pv = _np(np.asarray(vel, np.float32).reshape(-1, 3), np.float32)
+        force, pf = _np(np.asarray(force, np.float32).reshape(-1, 3), np.float32)
+        check(lib().lhmm_micro_set_state(self.h, int(box), pp, pv, pf, int(step),
+                                         float(le_offset)), "lhmm_micro_set_state")
+
+    def autotune(self, L_dev, probe_steps=10, stream=None):
+        check(lib().lhmm_micro_autotune(self.h, _ptr(L_dev), int(probe_steps),
+                                        _stream_ptr(stream)), "lhmm_micro_autotune")
+
+    def plan(self):
+        n = C.c_int()
+        check(lib().lhmm_micro_plan(self.h, C.byref(n), 0, None, None, None, None),
+              "lhmm_micro_plan")
+        k = n.value
+        arrs = [np.zeros(max(k, 1), np.int32) for _ in range(4)]
+        check(lib().lhmm_micro_plan(self.h, C.byref(n), k, *[a.ctypes.data_as(_I) for a in arrs]),
+              "lhmm_micro_plan")
+        return [dict(boxes=int(arrs[0][c]), max_beads=int(arrs[1][c]), threads=int(arrs[2][c]),
+                     min_blocks=int(arrs[3][c])) for c in range(k)]
+
+    def set_variant(self, cls, variant):
+        check(lib().lhmm_micro_set_variant(self.h, int(cls), int(variant)),
+              "lhmm_micro_set_variant")
+
+    def info(self):
+        nb = C.c_int()
+        tot = C.c_int64()
+        mx = C.c_int()
+        check(lib().lhmm_micro_info(self.h, C.byref(nb), C.byref(tot), C.byref(mx)),
+              "lhmm_micro_info")
+        return nb.value, tot.value, mx.value
