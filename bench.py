@@ -195,6 +195,8 @@ def main():
     ap.add_argument("--boxes", type=int, default=1024,
                     help="boxes of the workload (a smaller case for profilers)")
     ap.add_argument("--micro-steps", type=int, default=100, help="DPD steps per call")
+    ap.add_argument("--uniform-edge", type=float, default=0.0,
+                    help="give every box this edge (a one-class case for profilers)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -213,7 +215,11 @@ def main():
 
     global MICRO_STEPS
     MICRO_STEPS = args.micro_steps
-    batch = synth.batched_microsolver(n_boxes=args.boxes, seed=2 + rank)
+    if args.uniform_edge > 0:
+        batch = synth.make_batch(np.full(args.boxes, args.uniform_edge),
+                                 synth.random_velocity_gradients(args.boxes, 2 + rank), 2 + rank)
+    else:
+        batch = synth.batched_microsolver(n_boxes=args.boxes, seed=2 + rank)
     params = lhmm.dpd_params(flow="afbc", seed=2 + rank)
     micro = lhmm.Micro.from_batch(params, batch)
     stream = torch.cuda.current_stream()

@@ -274,7 +274,12 @@ __global__ void __launch_bounds__(T, MINB) micro_kernel(const MicroArgs A) {
         }
         ox[i] = o0; oy[i] = o1; oz[i] = o2;
         vx[i] = v0; vy[i] = v1; vz[i] = v2;
+        fx[i] = 0.f; fy[i] = 0.f; fz[i] = 0.f;  // re-accumulated in C
         cellid[i] = static_cast<unsigned short>(cx + nx * (cy + ny * cz));
+      }
+    } else {
+      for (int i = tid; i < N; i += T) {
+        fx[i] = 0.f; fy[i] = 0.f; fz[i] = 0.f;
       }
     }
     for (int c = tid; c < (C + 1) / 2; c += T) cnt32[c] = 0u;  // counters 0..C-1
@@ -340,10 +345,13 @@ __global__ void __launch_bounds__(T, MINB) micro_kernel(const MicroArgs A) {
     }
     __syncthreads();
 
-    // ---- C: forces and pair virial.  Each lane owns one bead per round and
-    // scans its 27 neighbour cells (9 rows of 3 x-cells, each row one or two
-    // contiguous slot ranges); pairs inside r_c go to the warp's queue and are
-    // evaluated 32 at a time with every lane busy.
+    // ---- C: forces and pair virial, each pair once (Newton's third law).
+    // Each lane owns one bead per round and scans the upper half of its
+    // neighbourhood: the rest of its own cell, the next x cell, and the rows
+    // (dz, dy) = (0,+1), (+1,-1), (+1,0), (+1,+1) of three x cells, each row
+    // one or two contiguous slot ranges.  Pairs inside r_c go to the warp's
+    // queue and are evaluated 32 at a time with every lane busy; f_i += F_ij
+    // and f_j -= F_ij with shared-memory atomics.
     float W[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     auto eval_pair = [&](unsigned long long e) {
       const int i = static_cast<int>(e & 0xffffu), j = static_cast<int>((e >> 16) & 0xffffu);
@@ -366,25 +374,29 @@ __global__ void __launch_bounds__(T, MINB) micro_kernel(const MicroArgs A) {
       const float th = lhmm::gauss_from_words(rr.x, rr.y);
       const float f = A.a * wR - A.gamma * wR * wR * ev + A.sig_dt * wR * th;
       const float fr = f * rinv;
-      atomicAdd(&fx[i], fr * rx);
-      atomicAdd(&fy[i], fr * ry);
-      atomicAdd(&fz[i], fr * rz);
+      const float Fx = fr * rx, Fy = fr * ry, Fz = fr * rz;
+      atomicAdd(&fx[i], Fx);
+      atomicAdd(&fy[i], Fy);
+      atomicAdd(&fz[i], Fz);
+      atomicAdd(&fx[j], -Fx);
+      atomicAdd(&fy[j], -Fy);
+      atomicAdd(&fz[j], -Fz);
       if (ikm) {
-        float wgt = 0.5f * fr;
+        float wgt = 1.f;
         if (ikm == 2) {
           int cx, cy, cz;
           cell_coords(cellid[i], nx, nxy, inx, inxy, cx, cy, cz);
           const float rpx = static_cast<float>(cx) * wx + ox[i] - hx;
           const float rpy = static_cast<float>(cy) * wy + oy[i] - hy;
           const float rpz = static_cast<float>(cz) * wz + oz[i] - hz;
-          wgt *= seg_fraction(rpx, rpy, rpz, rpx - rx, rpy - ry, rpz - rz, sB.half_core);
+          wgt = seg_fraction(rpx, rpy, rpz, rpx - rx, rpy - ry, rpz - rz, sB.half_core);
         }
-        W[0] += wgt * rx * rx;
-        W[1] += wgt * ry * ry;
-        W[2] += wgt * rz * rz;
-        W[3] += wgt * rx * ry;
-        W[4] += wgt * rx * rz;
-        W[5] += wgt * ry * rz;
+        W[0] += wgt * Fx * rx;
+        W[1] += wgt * Fy * ry;
+        W[2] += wgt * Fz * rz;
+        W[3] += wgt * Fx * ry;
+        W[4] += wgt * Fx * rz;
+        W[5] += wgt * Fy * rz;
       }
     };
 
@@ -407,63 +419,63 @@ __global__ void __launch_bounds__(T, MINB) micro_kernel(const MicroArgs A) {
                                 fmaxf(fabsf(rpy) - sB.half_core[1], fabsf(rpz) - sB.half_core[2]));
           ikm = (m >= A.rc) ? 0 : ((m < -A.rc) ? 1 : 2);
         }
-        float Fx = 0.f, Fy = 0.f, Fz = 0.f;
-        // FENE bonds (k, k+1) inside a chain, attractive (Eq. fene_force)
-        if (i < sB.n_poly) {
-#pragma unroll
-          for (int side = 0; side < 2; ++side) {
-            const int j = side == 0 ? i - 1 : i + 1;
-            const bool ok = side == 0 ? (i % A.chain_len) != 0 : ((i + 1) % A.chain_len) != 0;
-            if (!ok) continue;
-            int cxj, cyj, czj;
-            cell_coords(cellid[j], nx, nxy, inx, inxy, cxj, cyj, czj);
-            float rx = static_cast<float>(cx - cxj) * wx + (xi - ox[j]);
-            float ry = static_cast<float>(cy - cyj) * wy + (yi - oy[j]);
-            float rz = static_cast<float>(cz - czj) * wz + (zi - oz[j]);
-            if (ry > hy) {
-              ry -= sB.len[1];
-              if (le) rx -= le_off;
-            } else if (ry < -hy) {
-              ry += sB.len[1];
-              if (le) rx += le_off;
-            }
-            rx -= sB.len[0] * rintf(rx / sB.len[0]);
-            if (rz > hz) rz -= sB.len[2];
-            else if (rz < -hz) rz += sB.len[2];
-            float x = (rx * rx + ry * ry + rz * rz) * A.inv_R0sq;
-            if (!(x < 1.f)) {
-              status |= LHMM_BOX_BOND_OVERSTRETCH;
-              x = 0.99f;
-            }
-            const float cf = -A.H / (1.f - x);
-            Fx += cf * rx;
-            Fy += cf * ry;
-            Fz += cf * rz;
-            float wgt = 0.5f * cf;
-            if (afbc) {  // a bond is shorter than R0
-              const float m = fmaxf(fabsf(rpx) - sB.half_core[0],
-                                    fmaxf(fabsf(rpy) - sB.half_core[1], fabsf(rpz) - sB.half_core[2]));
-              if (m >= A.R0) wgt = 0.f;
-              else if (m >= -A.R0)
-                wgt *= seg_fraction(rpx, rpy, rpz, rpx - rx, rpy - ry, rpz - rz, sB.half_core);
-            }
-            W[0] += wgt * rx * rx;
-            W[1] += wgt * ry * ry;
-            W[2] += wgt * rz * rz;
-            W[3] += wgt * rx * ry;
-            W[4] += wgt * rx * rz;
-            W[5] += wgt * ry * rz;
+        // FENE bond (i, i+1) inside a chain, attractive (Eq. fene_force)
+        if (i + 1 < sB.n_poly && ((i + 1) % A.chain_len) != 0) {
+          const int j = i + 1;
+          int cxj, cyj, czj;
+          cell_coords(cellid[j], nx, nxy, inx, inxy, cxj, cyj, czj);
+          float rx = static_cast<float>(cx - cxj) * wx + (xi - ox[j]);
+          float ry = static_cast<float>(cy - cyj) * wy + (yi - oy[j]);
+          float rz = static_cast<float>(cz - czj) * wz + (zi - oz[j]);
+          if (ry > hy) {
+            ry -= sB.len[1];
+            if (le) rx -= le_off;
+          } else if (ry < -hy) {
+            ry += sB.len[1];
+            if (le) rx += le_off;
           }
+          rx -= sB.len[0] * rintf(rx / sB.len[0]);
+          if (rz > hz) rz -= sB.len[2];
+          else if (rz < -hz) rz += sB.len[2];
+          float x = (rx * rx + ry * ry + rz * rz) * A.inv_R0sq;
+          if (!(x < 1.f)) {
+            status |= LHMM_BOX_BOND_OVERSTRETCH;
+            x = 0.99f;
+          }
+          const float cf = -A.H / (1.f - x);
+          const float Fx = cf * rx, Fy = cf * ry, Fz = cf * rz;
+          atomicAdd(&fx[i], Fx);
+          atomicAdd(&fy[i], Fy);
+          atomicAdd(&fz[i], Fz);
+          atomicAdd(&fx[j], -Fx);
+          atomicAdd(&fy[j], -Fy);
+          atomicAdd(&fz[j], -Fz);
+          float wgt = 1.f;
+          if (afbc) {  // a bond is shorter than R0
+            const float m = fmaxf(fabsf(rpx) - sB.half_core[0],
+                                  fmaxf(fabsf(rpy) - sB.half_core[1], fabsf(rpz) - sB.half_core[2]));
+            if (m >= A.R0) wgt = 0.f;
+            else if (m >= -A.R0)
+              wgt = seg_fraction(rpx, rpy, rpz, rpx - rx, rpy - ry, rpz - rz, sB.half_core);
+          }
+          W[0] += wgt * Fx * rx;
+          W[1] += wgt * Fy * ry;
+          W[2] += wgt * Fz * rz;
+          W[3] += wgt * Fx * ry;
+          W[4] += wgt * Fx * rz;
+          W[5] += wgt * Fy * rz;
         }
-        fx[i] = Fx;
-        fy[i] = Fy;
-        fz[i] = Fz;
       }
-      __syncwarp();
-      for (int row = 0; row < 9; ++row) {
-        const int dz = row / 3 - 1, dy = row % 3 - 1;
-        int len1 = 0, len2 = 0, s1 = 0, s2 = 0, w1 = 0, w2 = 0, u1 = 0, u2 = 0, cross = 0;
-        int rowbase = 0;
+      // upper-half rows: (dz, dy) = (0,0) [own cell after slot k, next x cell],
+      // (0,+1), (+1,-1), (+1,0), (+1,+1) [three x cells each]
+      for (int row = 0; row < 5; ++row) {
+        const int dz = row < 2 ? 0 : 1;
+        const int dy = row == 0 ? 0 : (row == 1 ? 1 : row - 3);
+        // up to two slot ranges; inside a range, cell boundaries e0, e1 give
+        // the candidate's x cell as ua + (q >= e0) + (q >= e1)
+        int s1 = 0, len1 = 0, e01 = 0, e11 = 0, ua1 = 0;
+        int s2 = 0, len2 = 0, e02 = 0, e12 = 0, ua2 = 0;
+        int cross = 0;
         float sxr = 0.f;
         if (own) {
           const int z = wrapi(cz + dz, nz);
@@ -475,50 +487,62 @@ __global__ void __launch_bounds__(T, MINB) micro_kernel(const MicroArgs A) {
             y -= ny;
             if (le) { cross = 1; sxr = le_off; }
           }
-          rowbase = nx * (y + ny * z);
-          int ulo = cx - 1, uhi = cx + 1;
-          if (cross) {  // images slide by sxr: cells covering x_i - sxr +- rc
+          const int rowbase = nx * (y + ny * z);
+          int ulo, uhi;
+          if (row == 0) {
+            ulo = cx;
+            uhi = cx + 1;
+          } else if (cross) {  // images slide by sxr: cells covering x_i - sxr +- rc
             const float xt = static_cast<float>(cx) * wx + xi - sxr;
             ulo = static_cast<int>(floorf((xt - A.rc) * sB.winv[0]));
             uhi = min(static_cast<int>(floorf((xt + A.rc) * sB.winv[0])), ulo + 2);
+          } else {
+            ulo = cx - 1;
+            uhi = cx + 1;
           }
           const int wlo = ((ulo % nx) + nx) % nx, whi = ((uhi % nx) + nx) % nx;
           const bool single = (wlo <= whi) && (whi - wlo == uhi - ulo);
-          w1 = wlo;
-          u1 = ulo;
-          s1 = cstart[rowbase + wlo];
-          len1 = cstart[rowbase + (single ? whi : nx - 1) + 1] - s1;
+          const int wend1 = single ? whi : nx - 1;
+          ua1 = ulo;
+          s1 = (row == 0) ? k + 1 : cstart[rowbase + wlo];
+          e01 = cstart[rowbase + min(wlo + 1, wend1 + 1)];
+          e11 = cstart[rowbase + min(wlo + 2, wend1 + 1)];
+          if (wlo + 1 > wend1) e01 = 0x7fffffff;
+          if (wlo + 2 > wend1) e11 = 0x7fffffff;
+          len1 = cstart[rowbase + wend1 + 1] - s1;
           if (!single) {
-            w2 = 0;
-            u2 = uhi - whi;
+            ua2 = uhi - whi;
             s2 = cstart[rowbase];
+            e02 = whi >= 1 ? cstart[rowbase + 1] : 0x7fffffff;
+            e12 = whi >= 2 ? cstart[rowbase + 2] : 0x7fffffff;
             len2 = cstart[rowbase + whi + 1] - s2;
           }
         }
         const int len = len1 + len2;
         const int lmax = __reduce_max_sync(FULL, len);
+        const float byr = -static_cast<float>(dy) * wy, bzr = -static_cast<float>(dz) * wz;
         for (int t = 0; t < lmax; ++t) {
           bool hit = false;
-          unsigned long long ent = 0ull;
+          int q = 0, dcx = 0;
           if (t < len) {
             const bool first = t < len1;
-            const int q = first ? s1 + t : s2 + (t - len1);
+            q = first ? s1 + t : s2 + (t - len1);
+            const int e0 = first ? e01 : e02, e1 = first ? e11 : e12;
+            dcx = (first ? ua1 : ua2) + (q >= e0) + (q >= e1) - cx;
             const int j = perm[q];
-            const int cxj = static_cast<int>(cellid[j]) - rowbase;
-            const int dcx = (first ? u1 + (cxj - w1) : u2 + (cxj - w2)) - cx;
             const float rx = (-static_cast<float>(dcx) * wx - sxr) + (xi - ox[j]);
-            const float ry = -static_cast<float>(dy) * wy + (yi - oy[j]);
-            const float rz = -static_cast<float>(dz) * wz + (zi - oz[j]);
+            const float ry = byr + (yi - oy[j]);
+            const float rz = bzr + (zi - oz[j]);
             const float r2 = rx * rx + ry * ry + rz * rz;
-            hit = (r2 < A.rc2) && (r2 > 0.f) && (j != i);
+            hit = (r2 < A.rc2) && (r2 > 0.f);
             if (hit && !A.dpd_on_bonded) {
               const int lo = min(i, j), hi = max(i, j);
               if (hi == lo + 1 && hi < sB.n_poly && (hi % A.chain_len) != 0) hit = false;
             }
-            ent = pack_pair(i, j, dcx, dy, dz, ikm, cross);
+            q = j;
           }
           const unsigned bal = __ballot_sync(FULL, hit);
-          if (hit) queue[count + __popc(bal & lt_mask)] = ent;
+          if (hit) queue[count + __popc(bal & lt_mask)] = pack_pair(i, q, dcx, dy, dz, ikm, cross);
           count += __popc(bal);
           if (count >= 32) {
             __syncwarp();
