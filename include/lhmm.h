@@ -44,13 +44,15 @@ typedef enum {
   LHMM_ERR_CELL_OVERFLOW = 5,   /* a box outgrew its shared-memory plan */
   LHMM_ERR_NAN = 6,             /* a non-finite bead velocity or force */
   LHMM_ERR_TIMEOUT = 7,         /* a bounded device wait gave up */
-  LHMM_ERR_UNSUPPORTED = 8      /* a configuration this build does not run */
+  LHMM_ERR_UNSUPPORTED = 8,     /* a configuration this build does not run */
+  LHMM_ERR_FORCE_RANGE = 9      /* a pair force component exceeded 512 (clamped) */
 } lhmm_status;
 
 /* per-box device status bits, as returned by lhmm_micro_sync */
 #define LHMM_BOX_BOND_OVERSTRETCH 1u
 #define LHMM_BOX_NAN 2u
 #define LHMM_BOX_CELL_OVERFLOW 4u
+#define LHMM_BOX_FORCE_RANGE 8u
 
 /* imposed-flow treatment of the micro boxes */
 #define LHMM_FLOW_PERIODIC 0     /* plain periodic box, no imposed flow */
@@ -134,7 +136,7 @@ lhmm_status lhmm_micro_advance_host(lhmm_micro_t h, const float* L_host, int n_s
 /* Wait for the handle's stream work, read the per-box status words into
  * box_status_host (n_boxes uint32, or NULL), clear them, and return the first
  * error they hold (LHMM_ERR_BOND_OVERSTRETCH, LHMM_ERR_NAN,
- * LHMM_ERR_CELL_OVERFLOW) or LHMM_OK.  Synchronous. */
+ * LHMM_ERR_CELL_OVERFLOW, LHMM_ERR_FORCE_RANGE) or LHMM_OK.  Synchronous. */
 lhmm_status lhmm_micro_sync(lhmm_micro_t h, uint32_t* box_status_host);
 
 /* Copy one box's state to the host: absolute positions (n x 3 double; the

@@ -20,6 +20,7 @@ extern "C" const char* lhmm_status_string(lhmm_status s) {
     case LHMM_ERR_NAN: return "non-finite bead state";
     case LHMM_ERR_TIMEOUT: return "bounded device wait timed out";
     case LHMM_ERR_UNSUPPORTED: return "unsupported configuration";
+    case LHMM_ERR_FORCE_RANGE: return "pair force out of fixed-point range (clamped)";
   }
   return "unknown status";
 }

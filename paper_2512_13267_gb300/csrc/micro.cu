@@ -18,8 +18,9 @@
 //      micro_bc), accumulates the IK kinetic stress (Eq. kinetic_stress) and
 //      block-reduces the step's stress; the time average (N'_t = k') is kept
 //      in FP64.
-// Each pair is evaluated from both sides (no atomics, no cross-thread
-// writes), which keeps the force sums bit-reproducible.  The random term
+// Each pair is evaluated once (Newton's third law); pair forces accumulate in
+// 2^-18 fixed point with integer shared-memory atomics, which is exact and
+// order-independent, so a step is bit-reproducible.  The random term
 // theta_ij = theta_ji comes from Philox4x32-10 keyed by the box and counted
 // by (min id, max id, step), so it is identical from both sides and across
 // runs, and a checkpointed state resumes bit for bit.
@@ -76,6 +77,11 @@ struct MicroArgs {
 };
 
 constexpr int kRedFloats = 192;  // 6 x 32 warps, also scan scratch
+// Fixed-point pair-force accumulation: resolution 2^-18 (3.8e-6), each
+// contribution bounded by kFixMax, so a bead's sum stays far inside int32.
+constexpr float kFixScale = 262144.f;
+constexpr float kFixInv = 1.f / 262144.f;
+constexpr float kFixMax = 512.f;
 constexpr int kQueue = 64;       // pair-queue entries per warp
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
@@ -191,6 +197,11 @@ __global__ void __launch_bounds__(T, MINB) micro_kernel(const MicroArgs A) {
   float *ox = S.ox, *oy = S.oy, *oz = S.oz, *vx = S.vx, *vy = S.vy, *vz = S.vz;
   float *fx = S.fx, *fy = S.fy, *fz = S.fz;
   unsigned short *cellid = S.cellid, *perm = S.perm, *cstart = S.cstart;
+  // pair forces accumulate as 2^-18 fixed point in the force arrays (integer
+  // atomics: exact, so the sum does not depend on the order of the adds)
+  int* qfx = reinterpret_cast<int*>(fx);
+  int* qfy = reinterpret_cast<int*>(fy);
+  int* qfz = reinterpret_cast<int*>(fz);
 
   const long long off = sB.off;
   for (int i = tid; i < N; i += T) {
@@ -274,7 +285,7 @@ __global__ void __launch_bounds__(T, MINB) micro_kernel(const MicroArgs A) {
         }
         ox[i] = o0; oy[i] = o1; oz[i] = o2;
         vx[i] = v0; vy[i] = v1; vz[i] = v2;
-        fx[i] = 0.f; fy[i] = 0.f; fz[i] = 0.f;  // re-accumulated in C
+        fx[i] = 0.f; fy[i] = 0.f; fz[i] = 0.f;  // zero bits: fixed-point zero for C
         cellid[i] = static_cast<unsigned short>(cx + nx * (cy + ny * cz));
       }
     } else {
@@ -374,13 +385,24 @@ __global__ void __launch_bounds__(T, MINB) micro_kernel(const MicroArgs A) {
       const float th = lhmm::gauss_from_words(rr.x, rr.y);
       const float f = A.a * wR - A.gamma * wR * wR * ev + A.sig_dt * wR * th;
       const float fr = f * rinv;
-      const float Fx = fr * rx, Fy = fr * ry, Fz = fr * rz;
-      atomicAdd(&fx[i], Fx);
-      atomicAdd(&fy[i], Fy);
-      atomicAdd(&fz[i], Fz);
-      atomicAdd(&fx[j], -Fx);
-      atomicAdd(&fy[j], -Fy);
-      atomicAdd(&fz[j], -Fz);
+      float Fx = fr * rx, Fy = fr * ry, Fz = fr * rz;
+      if (!(fabsf(Fx) < kFixMax && fabsf(Fy) < kFixMax && fabsf(Fz) < kFixMax)) {
+        status |= LHMM_BOX_FORCE_RANGE;  // keep the fixed-point sums in range
+        Fx = fminf(fmaxf(Fx, -kFixMax), kFixMax);
+        Fy = fminf(fmaxf(Fy, -kFixMax), kFixMax);
+        Fz = fminf(fmaxf(Fz, -kFixMax), kFixMax);
+        if (Fx != Fx) Fx = 0.f;
+        if (Fy != Fy) Fy = 0.f;
+        if (Fz != Fz) Fz = 0.f;
+      }
+      const int ix = __float2int_rn(Fx * kFixScale), iy = __float2int_rn(Fy * kFixScale),
+                iz = __float2int_rn(Fz * kFixScale);
+      atomicAdd(&qfx[i], ix);
+      atomicAdd(&qfy[i], iy);
+      atomicAdd(&qfz[i], iz);
+      atomicAdd(&qfx[j], -ix);
+      atomicAdd(&qfy[j], -iy);
+      atomicAdd(&qfz[j], -iz);
       if (ikm) {
         float wgt = 1.f;
         if (ikm == 2) {
@@ -418,52 +440,6 @@ __global__ void __launch_bounds__(T, MINB) micro_kernel(const MicroArgs A) {
           const float m = fmaxf(fabsf(rpx) - sB.half_core[0],
                                 fmaxf(fabsf(rpy) - sB.half_core[1], fabsf(rpz) - sB.half_core[2]));
           ikm = (m >= A.rc) ? 0 : ((m < -A.rc) ? 1 : 2);
-        }
-        // FENE bond (i, i+1) inside a chain, attractive (Eq. fene_force)
-        if (i + 1 < sB.n_poly && ((i + 1) % A.chain_len) != 0) {
-          const int j = i + 1;
-          int cxj, cyj, czj;
-          cell_coords(cellid[j], nx, nxy, inx, inxy, cxj, cyj, czj);
-          float rx = static_cast<float>(cx - cxj) * wx + (xi - ox[j]);
-          float ry = static_cast<float>(cy - cyj) * wy + (yi - oy[j]);
-          float rz = static_cast<float>(cz - czj) * wz + (zi - oz[j]);
-          if (ry > hy) {
-            ry -= sB.len[1];
-            if (le) rx -= le_off;
-          } else if (ry < -hy) {
-            ry += sB.len[1];
-            if (le) rx += le_off;
-          }
-          rx -= sB.len[0] * rintf(rx / sB.len[0]);
-          if (rz > hz) rz -= sB.len[2];
-          else if (rz < -hz) rz += sB.len[2];
-          float x = (rx * rx + ry * ry + rz * rz) * A.inv_R0sq;
-          if (!(x < 1.f)) {
-            status |= LHMM_BOX_BOND_OVERSTRETCH;
-            x = 0.99f;
-          }
-          const float cf = -A.H / (1.f - x);
-          const float Fx = cf * rx, Fy = cf * ry, Fz = cf * rz;
-          atomicAdd(&fx[i], Fx);
-          atomicAdd(&fy[i], Fy);
-          atomicAdd(&fz[i], Fz);
-          atomicAdd(&fx[j], -Fx);
-          atomicAdd(&fy[j], -Fy);
-          atomicAdd(&fz[j], -Fz);
-          float wgt = 1.f;
-          if (afbc) {  // a bond is shorter than R0
-            const float m = fmaxf(fabsf(rpx) - sB.half_core[0],
-                                  fmaxf(fabsf(rpy) - sB.half_core[1], fabsf(rpz) - sB.half_core[2]));
-            if (m >= A.R0) wgt = 0.f;
-            else if (m >= -A.R0)
-              wgt = seg_fraction(rpx, rpy, rpz, rpx - rx, rpy - ry, rpz - rz, sB.half_core);
-          }
-          W[0] += wgt * Fx * rx;
-          W[1] += wgt * Fy * ry;
-          W[2] += wgt * Fz * rz;
-          W[3] += wgt * Fx * ry;
-          W[4] += wgt * Fx * rz;
-          W[5] += wgt * Fy * rz;
         }
       }
       // upper-half rows: (dz, dy) = (0,0) [own cell after slot k, next x cell],
@@ -558,6 +534,68 @@ __global__ void __launch_bounds__(T, MINB) micro_kernel(const MicroArgs A) {
     __syncwarp();
     if (lane < count) eval_pair(queue[lane]);
     __syncthreads();
+    for (int i = tid; i < N; i += T) {  // fixed point -> FP32
+      fx[i] = static_cast<float>(qfx[i]) * kFixInv;
+      fy[i] = static_cast<float>(qfy[i]) * kFixInv;
+      fz[i] = static_cast<float>(qfz[i]) * kFixInv;
+    }
+    __syncthreads();
+    // FENE bonds (k, k+1) inside a chain, attractive (Eq. fene_force); even
+    // then odd k so that no bead takes two bonds in one pass (plain adds,
+    // fixed order)
+    for (int par = 0; par < 2; ++par) {
+      for (int i = 2 * tid + par; i + 1 < sB.n_poly; i += 2 * T) {
+        if (((i + 1) % A.chain_len) == 0) continue;
+        const int j = i + 1;
+        int cx, cy, cz, cxj, cyj, czj;
+        cell_coords(cellid[i], nx, nxy, inx, inxy, cx, cy, cz);
+        cell_coords(cellid[j], nx, nxy, inx, inxy, cxj, cyj, czj);
+        float rx = static_cast<float>(cx - cxj) * wx + (ox[i] - ox[j]);
+        float ry = static_cast<float>(cy - cyj) * wy + (oy[i] - oy[j]);
+        float rz = static_cast<float>(cz - czj) * wz + (oz[i] - oz[j]);
+        if (ry > hy) {
+          ry -= sB.len[1];
+          if (le) rx -= le_off;
+        } else if (ry < -hy) {
+          ry += sB.len[1];
+          if (le) rx += le_off;
+        }
+        rx -= sB.len[0] * rintf(rx / sB.len[0]);
+        if (rz > hz) rz -= sB.len[2];
+        else if (rz < -hz) rz += sB.len[2];
+        float x = (rx * rx + ry * ry + rz * rz) * A.inv_R0sq;
+        if (!(x < 1.f)) {
+          status |= LHMM_BOX_BOND_OVERSTRETCH;
+          x = 0.99f;
+        }
+        const float cf = -A.H / (1.f - x);
+        const float Fx = cf * rx, Fy = cf * ry, Fz = cf * rz;
+        fx[i] += Fx;
+        fy[i] += Fy;
+        fz[i] += Fz;
+        fx[j] -= Fx;
+        fy[j] -= Fy;
+        fz[j] -= Fz;
+        float wgt = 1.f;
+        if (afbc) {  // a bond is shorter than R0
+          const float rpx = static_cast<float>(cx) * wx + ox[i] - hx;
+          const float rpy = static_cast<float>(cy) * wy + oy[i] - hy;
+          const float rpz = static_cast<float>(cz) * wz + oz[i] - hz;
+          const float m = fmaxf(fabsf(rpx) - sB.half_core[0],
+                                fmaxf(fabsf(rpy) - sB.half_core[1], fabsf(rpz) - sB.half_core[2]));
+          if (m >= A.R0) wgt = 0.f;
+          else if (m >= -A.R0)
+            wgt = seg_fraction(rpx, rpy, rpz, rpx - rx, rpy - ry, rpz - rz, sB.half_core);
+        }
+        W[0] += wgt * Fx * rx;
+        W[1] += wgt * Fy * ry;
+        W[2] += wgt * Fz * rz;
+        W[3] += wgt * Fx * ry;
+        W[4] += wgt * Fx * rz;
+        W[5] += wgt * Fy * rz;
+      }
+      __syncthreads();
+    }
     if (A.init_forces) break;
 
     // ---- D: second half kick, AFBC imposition, IK kinetic part, reduction
@@ -1065,6 +1103,7 @@ extern "C" lhmm_status lhmm_micro_sync(lhmm_micro_t h, uint32_t* box_status_host
   if (all & LHMM_BOX_BOND_OVERSTRETCH) return LHMM_ERR_BOND_OVERSTRETCH;
   if (all & LHMM_BOX_NAN) return LHMM_ERR_NAN;
   if (all & LHMM_BOX_CELL_OVERFLOW) return LHMM_ERR_CELL_OVERFLOW;
+  if (all & LHMM_BOX_FORCE_RANGE) return LHMM_ERR_FORCE_RANGE;
   return LHMM_OK;
 }
 

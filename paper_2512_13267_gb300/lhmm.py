@@ -14,8 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblhmm.so")
 
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_BOND_OVERSTRETCH, ERR_CELL_OVERFLOW, ERR_NAN, \
-    ERR_TIMEOUT, ERR_UNSUPPORTED = range(9)
-BOX_BOND_OVERSTRETCH, BOX_NAN, BOX_CELL_OVERFLOW = 1, 2, 4
+    ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_FORCE_RANGE = range(10)
+BOX_BOND_OVERSTRETCH, BOX_NAN, BOX_CELL_OVERFLOW, BOX_FORCE_RANGE = 1, 2, 4, 8
 FLOW_PERIODIC, FLOW_LEES_EDWARDS, FLOW_AFBC = 0, 1, 2
 FLOWS = {"periodic": FLOW_PERIODIC, "lees_edwards": FLOW_LEES_EDWARDS, "afbc": FLOW_AFBC}
 
