@@ -37,6 +37,11 @@ OPS_PER_BEAD = 35
 ALGO_OPS_PER_BEAD_STEP = PAIRS_PER_BEAD * OPS_PER_PAIR + OPS_PER_BEAD
 N_SM = 152
 LANES_PER_SM_CLK = 128
+# DRAM bytes (read + write) per bead and call of micro_kernel, from the ncu
+# capture in profiles/micro_kernel_e12_304box_full.md (91.3 MB for 1,575,936
+# beads); the kernel reads and writes box state once per call, so traffic
+# scales with beads, not with DPD steps.
+DRAM_BYTES_PER_BEAD_CALL = 91.316e6 / 1575936
 
 
 def _peaks():
@@ -280,7 +285,10 @@ def main():
     launch_s = (total_ms / args.steps) / 1e3
     achieved = per_launch_ops / launch_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
-                "frac": achieved / alu_peak, "traffic": None,
+                "frac": achieved / alu_peak,
+                "traffic": DRAM_BYTES_PER_BEAD_CALL * batch.total_beads,
+                "traffic_unit": "bytes per call (all size-class launches), scaled by beads from "
+                                "the 304-box capture",
                 "peak_source": "%d SMs x %d FP32/INT lanes x %.0f MHz (%s sm_max_mhz)"
                                % (N_SM, LANES_PER_SM_CLK, clk_mhz, src),
                 "kernel": "micro_kernel", "algo_ops_per_bead_step": ALGO_OPS_PER_BEAD_STEP}

@@ -183,6 +183,69 @@ lhmm_status lhmm_micro_plan(lhmm_micro_t h, int* n_classes, int cap, int* class_
  * LHMM_ERR_UNSUPPORTED if that variant's shared-memory plan does not fit. */
 lhmm_status lhmm_micro_set_variant(lhmm_micro_t h, int cls, int variant);
 
+/* ------------------------------------------------------------------------
+ * Macroscale SPH (Sec. 3.2, Eqs. sph_continuity and tait; Sec. 3.4,
+ * Eq. macro_micro).  2D periodic box [0,Lx) x [0,Ly); particles 0..n-n_wall-1
+ * are fluid and carry micro-domain (box) I = particle I; the last n_wall
+ * particles are fixed wall particles (v = 0) that take part in the density,
+ * pressure and viscous sums and carry no micro stress.
+ * ------------------------------------------------------------------------ */
+#define LHMM_SPH_WENDLAND_C2 0       /* W = 7/(pi h^2) (1+4q)(1-q)^4, support h */
+#define LHMM_SPH_LUCY 1              /* W = 5/(pi h^2) (1+3q)(1-q)^3 (Appendix A) */
+#define LHMM_SPH_VISC_DERIVED_2D 0   /* a = 2 eta - zeta, b = 4 zeta: shear viscosity eta in 2D */
+#define LHMM_SPH_VISC_PAPER_LITERAL 1/* a = 2 eta - zeta, b = 4 zeta + 2 eta as printed */
+#define LHMM_SPH_BODY_UNIFORM 0      /* body acceleration body_force everywhere */
+#define LHMM_SPH_BODY_REVERSE_POISEUILLE 1 /* +F_x for y >= Ly/2, -F_x below (Sec. 6.1) */
+
+typedef struct {
+  int n;            /* particles, walls included */
+  int n_wall;       /* the last n_wall particles are walls */
+  float Lx, Ly;     /* periodic box, each >= 2 h */
+  float h;          /* kernel support radius */
+  float mass;       /* particle mass m_I */
+  float rho0;       /* reference density of the Tait EOS */
+  float c;          /* artificial sound speed */
+  float theta_pb;   /* background pressure p_b = theta c^2 rho0 / 7 */
+  float eta_s;      /* solvent shear viscosity */
+  float zeta_s;     /* solvent bulk viscosity */
+  float dt;         /* SPH time step */
+  int kernel;       /* LHMM_SPH_WENDLAND_C2 | LHMM_SPH_LUCY */
+  int visc_coeffs;  /* LHMM_SPH_VISC_* */
+  float body_force[2]; /* body acceleration (x, y); F = body_force[0] for RPF */
+  int body_mode;    /* LHMM_SPH_BODY_* */
+} lhmm_sph_params;
+
+typedef struct lhmm_sph_s* lhmm_sph_t;
+
+/* Create from initial positions and velocities (host, n x 2 float; wall
+ * velocities are ignored) and compute the initial accelerations with zero
+ * micro stress.  Synchronous; allocates the particle state and its cell list. */
+lhmm_status lhmm_sph_create(const lhmm_sph_params* params, const float* pos0_host,
+                            const float* vel0_host, void* stream, lhmm_sph_t* out);
+lhmm_status lhmm_sph_destroy(lhmm_sph_t h);
+
+/* n_substeps velocity-Verlet SPH steps (coupling protocol Step 1) with the
+ * polymer stress held fixed, then, if L_out_dev != NULL, the velocity
+ * gradient of every fluid particle (Step 2).
+ *   stress_dev  device, (n - n_wall) x 6 double in the layout lhmm_micro_advance
+ *               writes (xx, yy, zz, xy, xz, yz; already scaled by alpha/lambda*),
+ *               or NULL for no micro stress.  Only xx, xy, yy enter the 2D sum.
+ *   L_out_dev   device, (n - n_wall) x 9 float, row-major L_ab = dv_a/dx_b with
+ *               the z row and column zero: the input lhmm_micro_advance takes.
+ * The first half kick uses the accelerations of the last force evaluation.
+ * Asynchronous on `stream`. */
+lhmm_status lhmm_sph_step(lhmm_sph_t h, const double* stress_dev, int n_substeps,
+                          float* L_out_dev, void* stream);
+
+/* Re-evaluate density, pressure and accelerations at the current state with
+ * the given stress (e.g. right after a new micro stress arrives).  Async. */
+lhmm_status lhmm_sph_recompute_forces(lhmm_sph_t h, const double* stress_dev, void* stream);
+
+/* Copy positions, velocities, accelerations (n x 2 float) and number
+ * densities (n float) to the host; any pointer may be NULL.  Synchronous. */
+lhmm_status lhmm_sph_get_state(lhmm_sph_t h, float* pos_host, float* vel_host, float* acc_host,
+                               float* density_host);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,422 @@
+// sph.cu -- macroscale SPH of the LHMM (arXiv 2512.13267, Sec. 3.2: Eqs.
+// sph_continuity and tait; Sec. 3.4: Eq. macro_micro) on sm_103a.
+//
+// 2D weakly compressible SPH in a periodic box.  Per substep: half kick and
+// drift (velocity-Verlet, coupling protocol Step 1), a counting-sort cell
+// list with cells >= h wide and ascending particle order inside each cell,
+// summation number density d_I = sum_J W_IJ (self included) with the Tait
+// pressure, and the momentum sum: pressure, Espanol-Revenga viscous pair
+// term with the half-step velocity, and the micro-stress coupling term
+// -(pi_I/d_I^2 + pi_J/d_J^2) F_IJ r_IJ, plus the body force; then the second
+// half kick.  After the substeps the velocity gradient of every fluid
+// particle, L_ab = dv_a/dx_b = sum_J (F_IJ/d_J) v_IJ,a r_IJ,b, is exported as
+// a 3x3 tensor for its micro-domain.  One thread per particle; every sum runs
+// in a fixed neighbour order, so a step is bit-reproducible.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "lhmm_common.cuh"
+
+namespace {
+
+struct SphArgs {
+  int n, n_fluid, ncx, ncy, ncell;
+  float Lx, Ly, cwx, cwy, h, hinv, mass, rho0, c2rho0_7, pb, a_visc, b_visc, dt;
+  int kernel, body_mode;
+  float bfx, bfy;
+  float2 *pos, *vel, *acc;
+  float *d, *p;
+  const int* wall;
+  int *cnt, *start, *perm, *cell_of;
+};
+
+__device__ __forceinline__ float kernel_W(int kind, float r, float h, float hinv) {
+  const float q = r * hinv;
+  if (q >= 1.f) return 0.f;
+  const float omq = 1.f - q;
+  const float inv_h2_pi = hinv * hinv * 0.318309886183790672f;  // 1/(pi h^2)
+  if (kind == LHMM_SPH_LUCY) return 5.f * inv_h2_pi * (1.f + 3.f * q) * omq * omq * omq;
+  return 7.f * inv_h2_pi * (1.f + 4.f * q) * omq * omq * omq * omq;
+}
+
+// F(r) = -W'(r)/r
+__device__ __forceinline__ float kernel_F(int kind, float r, float hinv) {
+  const float q = r * hinv;
+  if (q >= 1.f) return 0.f;
+  const float omq = 1.f - q;
+  const float h4 = hinv * hinv * hinv * hinv * 0.318309886183790672f;
+  if (kind == LHMM_SPH_LUCY) return 60.f * h4 * omq * omq;
+  return 140.f * h4 * omq * omq * omq;
+}
+
+__device__ __forceinline__ float2 min_image(float2 a, float2 b, float Lx, float Ly) {
+  float dx = a.x - b.x, dy = a.y - b.y;
+  dx -= Lx * rintf(dx / Lx);
+  dy -= Ly * rintf(dy / Ly);
+  return make_float2(dx, dy);
+}
+
+__device__ __forceinline__ int cell_index(float2 r, const SphArgs& A) {
+  int cx = static_cast<int>(floorf(r.x / A.cwx)), cy = static_cast<int>(floorf(r.y / A.cwy));
+  cx = min(max(cx, 0), A.ncx - 1);
+  cy = min(max(cy, 0), A.ncy - 1);
+  return cx + A.ncx * cy;
+}
+
+__global__ void sph_kick_drift(SphArgs A, float half_dt, int drift) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= A.n || A.wall[I]) return;
+  float2 v = A.vel[I];
+  const float2 a = A.acc[I];
+  v.x += half_dt * a.x;
+  v.y += half_dt * a.y;
+  A.vel[I] = v;
+  if (drift) {
+    float2 r = A.pos[I];
+    r.x += A.dt * v.x;
+    r.y += A.dt * v.y;
+    r.x -= A.Lx * floorf(r.x / A.Lx);
+    r.y -= A.Ly * floorf(r.y / A.Ly);
+    if (r.x >= A.Lx) r.x -= A.Lx;
+    if (r.y >= A.Ly) r.y -= A.Ly;
+    A.pos[I] = r;
+  }
+}
+
+// counting sort by cell in one block: count, scan, scatter, then ascending
+// particle order inside each cell
+__global__ void sph_cells(SphArgs A) {
+  __shared__ int warp_tot[32];
+  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  for (int c = tid; c < A.ncell; c += T) A.cnt[c] = 0;
+  __syncthreads();
+  for (int I = tid; I < A.n; I += T) {
+    const int c = cell_index(A.pos[I], A);
+    A.cell_of[I] = c;
+    atomicAdd(&A.cnt[c], 1);
+  }
+  __syncthreads();
+  const int per = (A.ncell + T - 1) / T;
+  const int c0 = min(tid * per, A.ncell), c1 = min(c0 + per, A.ncell);
+  int local = 0;
+  for (int c = c0; c < c1; ++c) local += A.cnt[c];
+  int x = local;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = T / 32;
+    int y = lane < nw ? warp_tot[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int z = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += z;
+    }
+    if (lane < nw) warp_tot[lane] = y;
+  }
+  __syncthreads();
+  int run = (warp > 0 ? warp_tot[warp - 1] : 0) + x - local;
+  for (int c = c0; c < c1; ++c) {
+    A.start[c] = run;
+    run += A.cnt[c];
+    A.cnt[c] = 0;
+  }
+  if (tid == 0) A.start[A.ncell] = A.n;
+  __syncthreads();
+  for (int I = tid; I < A.n; I += T) {
+    const int c = A.cell_of[I];
+    A.perm[A.start[c] + atomicAdd(&A.cnt[c], 1)] = I;
+  }
+  __syncthreads();
+  for (int c = tid; c < A.ncell; c += T) {
+    const int s0 = A.start[c], s1 = A.start[c + 1];
+    for (int q = s0 + 1; q < s1; ++q) {
+      const int key = A.perm[q];
+      int k = q - 1;
+      while (k >= s0 && A.perm[k] > key) {
+        A.perm[k + 1] = A.perm[k];
+        --k;
+      }
+      A.perm[k + 1] = key;
+    }
+  }
+}
+
+// visits the 3x3 cell neighbourhood of particle I in a fixed order
+template <typename F>
+__device__ __forceinline__ void for_neighbours(const SphArgs& A, int I, F&& fn) {
+  const int c = A.cell_of[I];
+  const int cx = c % A.ncx, cy = c / A.ncx;
+  for (int dy = -1; dy <= 1; ++dy) {
+    int y = cy + dy;
+    y += (y < 0) ? A.ncy : 0;
+    y -= (y >= A.ncy) ? A.ncy : 0;
+    for (int dx = -1; dx <= 1; ++dx) {
+      int x = cx + dx;
+      x += (x < 0) ? A.ncx : 0;
+      x -= (x >= A.ncx) ? A.ncx : 0;
+      const int cc = x + A.ncx * y;
+      const int e = A.start[cc + 1];
+      for (int q = A.start[cc]; q < e; ++q) fn(A.perm[q]);
+    }
+  }
+}
+
+__global__ void sph_density(SphArgs A) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= A.n) return;
+  const float2 ri = A.pos[I];
+  float s = 0.f;
+  for_neighbours(A, I, [&](int J) {
+    const float2 r = min_image(ri, A.pos[J], A.Lx, A.Ly);
+    s += kernel_W(A.kernel, sqrtf(r.x * r.x + r.y * r.y), A.h, A.hinv);
+  });
+  A.d[I] = s;
+  const float rr = A.mass * s / A.rho0;
+  const float r2 = rr * rr, r4 = r2 * r2;
+  A.p[I] = A.c2rho0_7 * (r4 * r2 * rr - 1.f) + A.pb;  // Eq. tait
+}
+
+__global__ void sph_force(SphArgs A, const double* stress) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= A.n) return;
+  if (A.wall[I]) {
+    A.acc[I] = make_float2(0.f, 0.f);
+    return;
+  }
+  const float2 ri = A.pos[I], vi = A.vel[I];
+  const float di = A.d[I], pi_ = A.p[I];
+  const float Pi = pi_ / (di * di);
+  float sxx = 0.f, sxy = 0.f, syy = 0.f;
+  if (stress && I < A.n_fluid) {
+    const float inv = 1.f / (di * di);
+    sxx = static_cast<float>(stress[6 * I + 0]) * inv;
+    syy = static_cast<float>(stress[6 * I + 1]) * inv;
+    sxy = static_cast<float>(stress[6 * I + 3]) * inv;
+  }
+  float fx = 0.f, fy = 0.f;
+  for_neighbours(A, I, [&](int J) {
+    if (J == I) return;
+    const float2 r = min_image(ri, A.pos[J], A.Lx, A.Ly);
+    const float rr = sqrtf(r.x * r.x + r.y * r.y);
+    const float F = kernel_F(A.kernel, rr, A.hinv);
+    if (F == 0.f || rr == 0.f) return;  // e_IJ undefined for coincident particles
+    const float dj = A.d[J];
+    const float P = Pi + A.p[J] / (dj * dj);
+    fx += P * F * r.x;
+    fy += P * F * r.y;
+    const float2 vj = A.vel[J];
+    const float vx = vi.x - vj.x, vy = vi.y - vj.y;
+    const float inv_r = 1.f / rr;
+    const float ex = r.x * inv_r, ey = r.y * inv_r;
+    const float ve = vx * ex + vy * ey;
+    const float cv = F / (di * dj);
+    fx -= (A.a_visc * vx + A.b_visc * ve * ex) * cv;
+    fy -= (A.a_visc * vy + A.b_visc * ve * ey) * cv;
+    if (stress) {
+      float jxx = sxx, jxy = sxy, jyy = syy;
+      if (J < A.n_fluid && !A.wall[J]) {
+        const float inv = 1.f / (dj * dj);
+        jxx += static_cast<float>(stress[6 * J + 0]) * inv;
+        jyy += static_cast<float>(stress[6 * J + 1]) * inv;
+        jxy += static_cast<float>(stress[6 * J + 3]) * inv;
+      }
+      fx -= (jxx * r.x + jxy * r.y) * F;
+      fy -= (jxy * r.x + jyy * r.y) * F;
+    }
+  });
+  float gx = A.bfx, gy = A.bfy;
+  if (A.body_mode == LHMM_SPH_BODY_REVERSE_POISEUILLE) {
+    gx = (ri.y >= 0.5f * A.Ly) ? A.bfx : -A.bfx;
+    gy = 0.f;
+  }
+  A.acc[I] = make_float2(fx / A.mass + gx, fy / A.mass + gy);
+}
+
+__global__ void sph_velgrad(SphArgs A, float* L_out) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= A.n_fluid) return;
+  const float2 ri = A.pos[I], vi = A.vel[I];
+  float Lxx = 0.f, Lxy = 0.f, Lyx = 0.f, Lyy = 0.f;
+  for_neighbours(A, I, [&](int J) {
+    if (J == I) return;
+    const float2 r = min_image(ri, A.pos[J], A.Lx, A.Ly);
+    const float F = kernel_F(A.kernel, sqrtf(r.x * r.x + r.y * r.y), A.hinv);
+    if (F == 0.f) return;
+    const float2 vj = A.vel[J];
+    const float cf = F / A.d[J];
+    const float vx = vi.x - vj.x, vy = vi.y - vj.y;
+    Lxx += cf * vx * r.x;
+    Lxy += cf * vx * r.y;
+    Lyx += cf * vy * r.x;
+    Lyy += cf * vy * r.y;
+  });
+  float* o = L_out + 9 * I;
+  o[0] = Lxx; o[1] = Lxy; o[2] = 0.f;
+  o[3] = Lyx; o[4] = Lyy; o[5] = 0.f;
+  o[6] = 0.f; o[7] = 0.f; o[8] = 0.f;
+}
+
+}  // namespace
+
+struct lhmm_sph_s {
+  lhmm_sph_params p;
+  SphArgs a;
+  int threads = 128;
+  cudaStream_t stream = nullptr;
+};
+
+namespace {
+
+void free_sph(lhmm_sph_t h) {
+  if (!h) return;
+  cudaFree(h->a.pos);
+  cudaFree(h->a.vel);
+  cudaFree(h->a.acc);
+  cudaFree(h->a.d);
+  cudaFree(h->a.p);
+  cudaFree(const_cast<int*>(h->a.wall));
+  cudaFree(h->a.cnt);
+  cudaFree(h->a.start);
+  cudaFree(h->a.perm);
+  cudaFree(h->a.cell_of);
+  delete h;
+}
+
+cudaError_t eval_forces(lhmm_sph_s* h, const double* stress, cudaStream_t s) {
+  const int T = h->threads, G = (h->a.n + T - 1) / T;
+  sph_cells<<<1, 1024, 0, s>>>(h->a);
+  sph_density<<<G, T, 0, s>>>(h->a);
+  sph_force<<<G, T, 0, s>>>(h->a, stress);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" lhmm_status lhmm_sph_create(const lhmm_sph_params* params, const float* pos0_host,
+                                       const float* vel0_host, void* stream, lhmm_sph_t* out) {
+  if (!params || !out || !pos0_host || !vel0_host) return LHMM_ERR_ARG;
+  *out = nullptr;
+  const lhmm_sph_params& p = *params;
+  if (p.n <= 0 || p.n_wall < 0 || p.n_wall > p.n || !(p.h > 0.f) || !(p.Lx >= 2.f * p.h) ||
+      !(p.Ly >= 2.f * p.h) || !(p.mass > 0.f) || !(p.rho0 > 0.f) || !(p.dt > 0.f) ||
+      (p.kernel != LHMM_SPH_WENDLAND_C2 && p.kernel != LHMM_SPH_LUCY))
+    return LHMM_ERR_ARG;
+  lhmm_sph_s* h = new lhmm_sph_s();
+  h->p = p;
+  h->stream = static_cast<cudaStream_t>(stream);
+  SphArgs& a = h->a;
+  a.n = p.n;
+  a.n_fluid = p.n - p.n_wall;
+  a.ncx = std::max(3, static_cast<int>(std::floor(p.Lx / p.h)));
+  a.ncy = std::max(3, static_cast<int>(std::floor(p.Ly / p.h)));
+  a.ncell = a.ncx * a.ncy;
+  a.Lx = p.Lx;
+  a.Ly = p.Ly;
+  a.cwx = p.Lx / a.ncx;
+  a.cwy = p.Ly / a.ncy;
+  a.h = p.h;
+  a.hinv = 1.f / p.h;
+  a.mass = p.mass;
+  a.rho0 = p.rho0;
+  a.c2rho0_7 = p.c * p.c * p.rho0 / 7.f;
+  a.pb = p.theta_pb * p.c * p.c * p.rho0 / 7.f;
+  a.a_visc = 2.f * p.eta_s - p.zeta_s;
+  a.b_visc = (p.visc_coeffs == LHMM_SPH_VISC_PAPER_LITERAL) ? 4.f * p.zeta_s + 2.f * p.eta_s
+                                                            : 4.f * p.zeta_s;
+  a.dt = p.dt;
+  a.kernel = p.kernel;
+  a.body_mode = p.body_mode;
+  a.bfx = p.body_force[0];
+  a.bfy = p.body_force[1];
+  const size_t n = static_cast<size_t>(p.n);
+  std::vector<int> wall(n, 0);
+  for (size_t I = static_cast<size_t>(a.n_fluid); I < n; ++I) wall[I] = 1;  // walls come last
+  cudaError_t e;
+  int* wall_d = nullptr;
+  if ((e = cudaMalloc(&a.pos, sizeof(float2) * n)) != cudaSuccess ||
+      (e = cudaMalloc(&a.vel, sizeof(float2) * n)) != cudaSuccess ||
+      (e = cudaMalloc(&a.acc, sizeof(float2) * n)) != cudaSuccess ||
+      (e = cudaMalloc(&a.d, sizeof(float) * n)) != cudaSuccess ||
+      (e = cudaMalloc(&a.p, sizeof(float) * n)) != cudaSuccess ||
+      (e = cudaMalloc(&wall_d, sizeof(int) * n)) != cudaSuccess ||
+      (e = cudaMalloc(&a.cnt, sizeof(int) * a.ncell)) != cudaSuccess ||
+      (e = cudaMalloc(&a.start, sizeof(int) * (a.ncell + 1))) != cudaSuccess ||
+      (e = cudaMalloc(&a.perm, sizeof(int) * n)) != cudaSuccess ||
+      (e = cudaMalloc(&a.cell_of, sizeof(int) * n)) != cudaSuccess) {
+    a.wall = wall_d;
+    free_sph(h);
+    return lhmm_cuda_error(e);
+  }
+  a.wall = wall_d;
+  std::vector<float2> pos(n), vel(n);
+  for (size_t I = 0; I < n; ++I) {
+    float x = pos0_host[2 * I], y = pos0_host[2 * I + 1];
+    x -= p.Lx * std::floor(x / p.Lx);
+    y -= p.Ly * std::floor(y / p.Ly);
+    pos[I] = make_float2(x, y);
+    vel[I] = wall[I] ? make_float2(0.f, 0.f) : make_float2(vel0_host[2 * I], vel0_host[2 * I + 1]);
+  }
+  cudaStream_t s = h->stream;
+  if ((e = cudaMemcpyAsync(a.pos, pos.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(a.vel, vel.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(wall_d, wall.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = eval_forces(h, nullptr, s)) != cudaSuccess || (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+    free_sph(h);
+    return lhmm_cuda_error(e);
+  }
+  *out = h;
+  return LHMM_OK;
+}
+
+extern "C" lhmm_status lhmm_sph_destroy(lhmm_sph_t h) {
+  if (!h) return LHMM_ERR_ARG;
+  cudaDeviceSynchronize();
+  free_sph(h);
+  return LHMM_OK;
+}
+
+extern "C" lhmm_status lhmm_sph_step(lhmm_sph_t h, const double* stress_dev, int n_substeps,
+                                     float* L_out_dev, void* stream) {
+  if (!h || n_substeps < 0) return LHMM_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int T = h->threads, G = (h->a.n + T - 1) / T;
+  const float half = 0.5f * h->p.dt;
+  for (int k = 0; k < n_substeps; ++k) {
+    sph_kick_drift<<<G, T, 0, s>>>(h->a, half, 1);
+    LHMM_CK(eval_forces(h, stress_dev, s));
+    sph_kick_drift<<<G, T, 0, s>>>(h->a, half, 0);
+  }
+  if (L_out_dev) {
+    if (n_substeps == 0) {  // density of the current positions
+      sph_cells<<<1, 1024, 0, s>>>(h->a);
+      sph_density<<<G, T, 0, s>>>(h->a);
+    }
+    const int Gf = (h->a.n_fluid + T - 1) / T;
+    if (Gf > 0) sph_velgrad<<<Gf, T, 0, s>>>(h->a, L_out_dev);
+  }
+  LHMM_CK(cudaGetLastError());
+  return LHMM_OK;
+}
+
+extern "C" lhmm_status lhmm_sph_recompute_forces(lhmm_sph_t h, const double* stress_dev,
+                                                 void* stream) {
+  if (!h) return LHMM_ERR_ARG;
+  LHMM_CK(eval_forces(h, stress_dev, static_cast<cudaStream_t>(stream)));
+  return LHMM_OK;
+}
+
+extern "C" lhmm_status lhmm_sph_get_state(lhmm_sph_t h, float* pos_host, float* vel_host,
+                                          float* acc_host, float* density_host) {
+  if (!h) return LHMM_ERR_ARG;
+  LHMM_CK(cudaDeviceSynchronize());
+  const size_t n = static_cast<size_t>(h->a.n);
+  if (pos_host) LHMM_CK(cudaMemcpy(pos_host, h->a.pos, sizeof(float2) * n, cudaMemcpyDeviceToHost));
+  if (vel_host) LHMM_CK(cudaMemcpy(vel_host, h->a.vel, sizeof(float2) * n, cudaMemcpyDeviceToHost));
+  if (acc_host) LHMM_CK(cudaMemcpy(acc_host, h->a.acc, sizeof(float2) * n, cudaMemcpyDeviceToHost));
+  if (density_host) LHMM_CK(cudaMemcpy(density_host, h->a.d, sizeof(float) * n, cudaMemcpyDeviceToHost));
+  return LHMM_OK;
+}

@@ -42,6 +42,20 @@ class BatchDesc(C.Structure):
                 ("chain_len", C.c_int)]
 
 
+class SphParams(C.Structure):
+    _fields_ = [
+        ("n", C.c_int), ("n_wall", C.c_int), ("Lx", C.c_float), ("Ly", C.c_float),
+        ("h", C.c_float), ("mass", C.c_float), ("rho0", C.c_float), ("c", C.c_float),
+        ("theta_pb", C.c_float), ("eta_s", C.c_float), ("zeta_s", C.c_float), ("dt", C.c_float),
+        ("kernel", C.c_int), ("visc_coeffs", C.c_int), ("body_force", C.c_float * 2),
+        ("body_mode", C.c_int),
+    ]
+
+
+SPH_WENDLAND_C2, SPH_LUCY = 0, 1
+SPH_VISC_DERIVED_2D, SPH_VISC_PAPER_LITERAL = 0, 1
+SPH_BODY_UNIFORM, SPH_BODY_REVERSE_POISEUILLE = 0, 1
+
 _lib = None
 _F = C.POINTER(C.c_float)
 _D = C.POINTER(C.c_double)
@@ -72,6 +86,11 @@ def lib():
         L.lhmm_micro_autotune.argtypes = [vp, vp, C.c_int, vp]
         L.lhmm_micro_plan.argtypes = [vp, _I, C.c_int, _I, _I, _I, _I]
         L.lhmm_micro_set_variant.argtypes = [vp, C.c_int, C.c_int]
+        L.lhmm_sph_create.argtypes = [C.POINTER(SphParams), _F, _F, vp, C.POINTER(vp)]
+        L.lhmm_sph_destroy.argtypes = [vp]
+        L.lhmm_sph_step.argtypes = [vp, vp, C.c_int, vp, vp]
+        L.lhmm_sph_recompute_forces.argtypes = [vp, vp, vp]
+        L.lhmm_sph_get_state.argtypes = [vp, _F, _F, _F, _F]
         _lib = L
     return _lib
 
@@ -233,3 +252,58 @@ class Micro:
         check(lib().lhmm_micro_info(self.h, C.byref(nb), C.byref(tot), C.byref(mx)),
               "lhmm_micro_info")
         return nb.value, tot.value, mx.value
+
+
+def sph_params(n, n_wall=0, **kw):
+    d = dict(Lx=1.0, Ly=1.0, h=0.3, mass=1.0, rho0=1.0, c=1.0, theta_pb=0.1, eta_s=0.1,
+             zeta_s=0.0, dt=1e-3, kernel=SPH_WENDLAND_C2, visc_coeffs=SPH_VISC_DERIVED_2D,
+             body_mode=SPH_BODY_UNIFORM)
+    bf = kw.pop("body_force", (0.0, 0.0))
+    d.update(kw)
+    p = SphParams(n=int(n), n_wall=int(n_wall), **d)
+    p.body_force[0], p.body_force[1] = bf
+    return p
+
+
+class Sph:
+    """Macroscale SPH particles resident on the GPU (lhmm_sph_*)."""
+
+    def __init__(self, params, pos0, vel0, stream=None):
+        pos0, pp = _np(np.asarray(pos0, np.float32).reshape(-1, 2), np.float32)
+        vel0, pv = _np(np.asarray(vel0, np.float32).reshape(-1, 2), np.float32)
+        self.params = params
+        self.n = int(params.n)
+        self.n_fluid = int(params.n - params.n_wall)
+        h = C.c_void_p()
+        check(lib().lhmm_sph_create(C.byref(params), pp, pv, _stream_ptr(stream), C.byref(h)),
+              "lhmm_sph_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lhmm_sph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n_substeps, stress_dev=None, L_out_dev=None, stream=None):
+        check(lib().lhmm_sph_step(self.h, _ptr(stress_dev), int(n_substeps), _ptr(L_out_dev),
+                                  _stream_ptr(stream)), "lhmm_sph_step")
+
+    def recompute_forces(self, stress_dev=None, stream=None):
+        check(lib().lhmm_sph_recompute_forces(self.h, _ptr(stress_dev), _stream_ptr(stream)),
+              "lhmm_sph_recompute_forces")
+
+    def get_state(self):
+        pos = np.zeros((self.n, 2), np.float32)
+        vel = np.zeros((self.n, 2), np.float32)
+        acc = np.zeros((self.n, 2), np.float32)
+        d = np.zeros(self.n, np.float32)
+        check(lib().lhmm_sph_get_state(self.h, pos.ctypes.data_as(_F), vel.ctypes.data_as(_F),
+                                       acc.ctypes.data_as(_F), d.ctypes.data_as(_F)),
+              "lhmm_sph_get_state")
+        return pos, vel, acc, d
