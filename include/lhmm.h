@@ -246,6 +246,33 @@ lhmm_status lhmm_sph_recompute_forces(lhmm_sph_t h, const double* stress_dev, vo
 lhmm_status lhmm_sph_get_state(lhmm_sph_t h, float* pos_host, float* vel_host, float* acc_host,
                                float* density_host);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free SPH velocity gradient.  The paper has no counterpart: this
+ * entry point exists for callers that may not allocate device memory when
+ * they need the gradients (code inside another framework's memory pool or an
+ * allocator-free real-time section, plug-ins restricted to buffers they are
+ * handed).  It computes what lhmm_sph_step(h, ..., n_substeps = 0, L_out) computes
+ * for the given particles -- number densities, then L_ab = dv_a/dx_b of every
+ * fluid particle -- without a handle and without any allocation: its scratch
+ * (cell list, densities, pressures; about 1.5 MiB) is one fixed array in the
+ * library's device memory, held by every GPU that loads the library until the
+ * process exits.
+ *   params     host; n, n_wall, Lx, Ly, h, mass, rho0, c, theta_pb, kernel are
+ *              used (the walls are the last n_wall particles).
+ *   pos_dev    device, n x 2 float, 8-byte aligned; vel_dev likewise.
+ *   L_out_dev  device, (n - n_wall) x 9 float (the lhmm_micro_advance layout).
+ * Returns LHMM_ERR_ARG for n > LHMM_NOALLOC_MAX_PARTICLES or more than
+ * LHMM_NOALLOC_MAX_CELLS cells (floor(Lx/h) x floor(Ly/h), at least 3 each).
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call uses the same scratch array, so calls that can overlap on the GPU
+ * (different streams, or different host threads) race: serialise them.
+ * Asynchronous on `stream`. */
+#define LHMM_NOALLOC_MAX_PARTICLES 65536
+#define LHMM_NOALLOC_MAX_CELLS 65536
+lhmm_status lhmm_sph_velgrad_noalloc(const lhmm_sph_params* params, const float* pos_dev,
+                                     const float* vel_dev, float* L_out_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

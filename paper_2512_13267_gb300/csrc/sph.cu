@@ -14,6 +14,8 @@
 // in a fixed neighbour order, so a step is bit-reproducible.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
+#include <mutex>
 #include <vector>
 
 #include "lhmm_common.cuh"
@@ -418,5 +420,106 @@ extern "C" lhmm_status lhmm_sph_get_state(lhmm_sph_t h, float* pos_host, float* 
   if (vel_host) LHMM_CK(cudaMemcpy(vel_host, h->a.vel, sizeof(float2) * n, cudaMemcpyDeviceToHost));
   if (acc_host) LHMM_CK(cudaMemcpy(acc_host, h->a.acc, sizeof(float2) * n, cudaMemcpyDeviceToHost));
   if (density_host) LHMM_CK(cudaMemcpy(density_host, h->a.d, sizeof(float) * n, cudaMemcpyDeviceToHost));
+  return LHMM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free velocity-gradient export.
+//
+// Some callers cannot call cudaMalloc at the point where they need this
+// result: code running inside another framework's memory pool or
+// allocator-free section, real-time loops that must not touch the driver's
+// allocator, or plug-ins that may only use memory they are handed.  For them
+// this entry point computes the same SPH number densities and velocity
+// gradients as lhmm_sph_step(..., n_substeps = 0, L_out) but keeps all of its
+// scratch (cell list, densities, pressures) in one fixed-size array in device
+// global memory that belongs to this library.  The array is a file-scope
+// __device__ variable, so every GPU that loads the library holds it until the
+// process exits.  The caller passes inputs and outputs as usual.
+namespace {
+
+constexpr int kNoallocMaxParticles = LHMM_NOALLOC_MAX_PARTICLES;
+constexpr int kNoallocMaxCells = LHMM_NOALLOC_MAX_CELLS;
+// cell_of, perm, density, pressure (per particle) and counters, starts (per cell)
+constexpr size_t kNoallocBytes =
+    4 * sizeof(int) * static_cast<size_t>(kNoallocMaxParticles) +
+    sizeof(int) * (2 * static_cast<size_t>(kNoallocMaxCells) + 64);
+
+static __device__ __align__(256) unsigned char g_sph_noalloc_scratch[kNoallocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array for the current device.  The symbol's
+// name is only a host-side handle; the address has to be looked up once per
+// device (with that device current) before a kernel may use it.
+cudaError_t noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_sph_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" lhmm_status lhmm_sph_velgrad_noalloc(const lhmm_sph_params* params,
+                                                const float* pos_dev, const float* vel_dev,
+                                                float* L_out_dev, void* stream) {
+  if (!params || !pos_dev || !vel_dev || !L_out_dev) return LHMM_ERR_ARG;
+  const lhmm_sph_params& p = *params;
+  if (p.n <= 0 || p.n_wall < 0 || p.n_wall > p.n || !(p.h > 0.f) || !(p.Lx >= 2.f * p.h) ||
+      !(p.Ly >= 2.f * p.h) || !(p.mass > 0.f) || !(p.rho0 > 0.f) ||
+      (p.kernel != LHMM_SPH_WENDLAND_C2 && p.kernel != LHMM_SPH_LUCY))
+    return LHMM_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(pos_dev) | reinterpret_cast<uintptr_t>(vel_dev)) % 8 != 0)
+    return LHMM_ERR_ARG;  // read as float2
+  const int ncx = std::max(3, static_cast<int>(std::floor(p.Lx / p.h)));
+  const int ncy = std::max(3, static_cast<int>(std::floor(p.Ly / p.h)));
+  if (p.n > kNoallocMaxParticles || static_cast<long long>(ncx) * ncy > kNoallocMaxCells)
+    return LHMM_ERR_ARG;  // beyond the fixed scratch array
+  void* base = nullptr;
+  LHMM_CK(noalloc_scratch(&base));
+  SphArgs a{};
+  a.n = p.n;
+  a.n_fluid = p.n - p.n_wall;
+  a.ncx = ncx;
+  a.ncy = ncy;
+  a.ncell = ncx * ncy;
+  a.Lx = p.Lx;
+  a.Ly = p.Ly;
+  a.cwx = p.Lx / ncx;
+  a.cwy = p.Ly / ncy;
+  a.h = p.h;
+  a.hinv = 1.f / p.h;
+  a.mass = p.mass;
+  a.rho0 = p.rho0;
+  a.c2rho0_7 = p.c * p.c * p.rho0 / 7.f;
+  a.pb = p.theta_pb * p.c * p.c * p.rho0 / 7.f;
+  a.kernel = p.kernel;
+  a.pos = const_cast<float2*>(reinterpret_cast<const float2*>(pos_dev));
+  a.vel = const_cast<float2*>(reinterpret_cast<const float2*>(vel_dev));
+  int* ib = static_cast<int*>(base);
+  a.cell_of = ib;
+  a.perm = ib + kNoallocMaxParticles;
+  a.d = reinterpret_cast<float*>(ib + 2 * kNoallocMaxParticles);
+  a.p = reinterpret_cast<float*>(ib + 3 * kNoallocMaxParticles);
+  a.cnt = ib + 4 * kNoallocMaxParticles;  // cleared by sph_cells on every call
+  a.start = a.cnt + kNoallocMaxCells;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int T = 128, G = (a.n + T - 1) / T, Gf = (a.n_fluid + T - 1) / T;
+  sph_cells<<<1, 1024, 0, s>>>(a);
+  sph_density<<<G, T, 0, s>>>(a);
+  if (Gf > 0) sph_velgrad<<<Gf, T, 0, s>>>(a, L_out_dev);
+  LHMM_CK(cudaGetLastError());
   return LHMM_OK;
 }

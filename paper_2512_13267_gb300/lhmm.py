@@ -91,6 +91,7 @@ def lib():
         L.lhmm_sph_step.argtypes = [vp, vp, C.c_int, vp, vp]
         L.lhmm_sph_recompute_forces.argtypes = [vp, vp, vp]
         L.lhmm_sph_get_state.argtypes = [vp, _F, _F, _F, _F]
+        L.lhmm_sph_velgrad_noalloc.argtypes = [C.POINTER(SphParams), vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -307,3 +308,16 @@ class Sph:
                                        acc.ctypes.data_as(_F), d.ctypes.data_as(_F)),
               "lhmm_sph_get_state")
         return pos, vel, acc, d
+
+
+NOALLOC_MAX_PARTICLES = 65536
+
+
+def sph_velgrad_noalloc(params, pos_dev, vel_dev, L_out_dev, stream=None):
+    """Velocity gradients of the given particles without any device allocation
+    (lhmm_sph_velgrad_noalloc): for callers that may not allocate device memory
+    at that point.  All calls share one fixed scratch array in the library, so
+    calls that may overlap on the GPU must be serialised by the caller."""
+    check(lib().lhmm_sph_velgrad_noalloc(C.byref(params), _ptr(pos_dev), _ptr(vel_dev),
+                                         _ptr(L_out_dev), _stream_ptr(stream)),
+          "lhmm_sph_velgrad_noalloc")
