@@ -146,6 +146,54 @@ def cpu_oracle_rate(batch, budget_s=12.0, min_s=6.0, chunk_steps=5, n_boxes=24):
     return rate, threads, desc
 
 
+def macro_step_rate(steps=10, warmup=2):
+    """LHMM macro-steps/s of the coupled reverse-Poiseuille channel (64 x 32 SPH
+    particles, one 1500-bead AFBC box each, k' = 50 DPD steps per macro step,
+    M SPH substeps from the CFL rule), graph-captured macro steps."""
+    import torch
+    from paper_2512_13267_gb300 import lhmm, synth
+    U_o, c_fac, eta_s, alpha, k_micro, dt_dpd = 1.0, 10.0, 0.5, 0.01, 50, 0.01
+    sph_cfg, batch = synth.coupled_channel(U_o=U_o, c_factor=c_fac, eta_s=eta_s,
+                                           eta_tot=eta_s + 0.01)
+    delta_t = k_micro * dt_dpd                    # exchange interval (lambda* = 1)
+    dt_cfl = 0.25 * sph_cfg["h"] / (1.5 * U_o + sph_cfg["c"])
+    M = int(np.ceil(delta_t / dt_cfl))
+    sp = lhmm.sph_params(sph_cfg["pos"].shape[0], 0, Lx=sph_cfg["Lx"], Ly=sph_cfg["Ly"],
+                         h=sph_cfg["h"], mass=sph_cfg["mass"], rho0=1.0, c=sph_cfg["c"],
+                         theta_pb=0.1, eta_s=eta_s, dt=delta_t / M,
+                         body_force=(sph_cfg["body_force"], 0.0),
+                         body_mode=lhmm.SPH_BODY_REVERSE_POISEUILLE)
+    sph = lhmm.Sph(sp, sph_cfg["pos"], sph_cfg["vel"])
+    micro = lhmm.Micro.from_batch(lhmm.dpd_params(flow="afbc", seed=3, alpha=alpha), batch)
+    L0 = torch.zeros((batch.n_boxes, 9), dtype=torch.float32, device="cuda")
+    micro.autotune(L0, probe_steps=10)
+    cpl = lhmm.Coupled(sph, micro, M, k_micro)
+    stream = torch.cuda.current_stream()
+    cpl.step(warmup, use_graph=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    cpl.step(steps, use_graph=True)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    status, _ = micro.sync(raise_on_error=False)
+    out = {"metric": "LHMM macro-steps/s (plain DPD closure)", "value": steps / (ms / 1e3),
+           "unit": "macro-steps/s", "ms_per_macro_step": ms / steps, "steps": steps,
+           "warmup": warmup, "sph_particles": int(sph_cfg["pos"].shape[0]),
+           "sph_substeps": M, "micro_steps": k_micro, "boxes": batch.n_boxes,
+           "beads": batch.total_beads,
+           "bead_steps_per_s": batch.total_beads * k_micro * steps / (ms / 1e3),
+           "cuda_graph": True, "device_status": lhmm.status_string(status),
+           "workload": "coupled reverse-Poiseuille channel 64x32 SPH (Ly=4, h=3dh, Wendland, "
+                       "c=10 U_o) x 1500-bead AFBC boxes, k'=50, M=%d" % M}
+    cpl.close()
+    micro.close()
+    sph.close()
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -200,6 +248,7 @@ def main():
     ap.add_argument("--boxes", type=int, default=1024,
                     help="boxes of the workload (a smaller case for profilers)")
     ap.add_argument("--micro-steps", type=int, default=100, help="DPD steps per call")
+    ap.add_argument("--no-macro", action="store_true", help="skip the coupled macro-step line")
     ap.add_argument("--uniform-edge", type=float, default=0.0,
                     help="give every box this edge (a one-class case for profilers)")
     args = ap.parse_args()
@@ -309,6 +358,8 @@ def main():
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": desc}
     micro.close()
+    if rank == 0 and not args.no_macro and args.uniform_edge <= 0:
+        line["secondary"] = macro_step_rate()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

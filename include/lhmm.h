@@ -246,6 +246,39 @@ lhmm_status lhmm_sph_recompute_forces(lhmm_sph_t h, const double* stress_dev, vo
 lhmm_status lhmm_sph_get_state(lhmm_sph_t h, float* pos_host, float* vel_host, float* acc_host,
                                float* density_host);
 
+/* Particle counts of an SPH handle. */
+lhmm_status lhmm_sph_info(lhmm_sph_t h, int* n, int* n_wall);
+
+/* ------------------------------------------------------------------------
+ * The coupled macro step (coupling protocol, Steps 1-4; time coupling
+ * delta_t = M dt_SPH = k' dt_DPD, Eq. in Sec. 3.3.1).  Ties one SPH handle to
+ * one micro handle with a box per fluid particle (box I <-> particle I).  One
+ * macro step: lhmm_sph_step with the current polymer stress and M substeps,
+ * writing the velocity gradients; then lhmm_micro_advance of every box by k'
+ * steps under them, writing the new stress.  The two exchange buffers are
+ * device arrays owned by the coupled handle.  The caller keeps ownership of
+ * the SPH and micro handles and must keep them alive.
+ * ------------------------------------------------------------------------ */
+typedef struct lhmm_coupled_s* lhmm_coupled_t;
+
+lhmm_status lhmm_coupled_create(lhmm_sph_t sph, lhmm_micro_t micro, int sph_substeps,
+                                int micro_steps, lhmm_coupled_t* out);
+lhmm_status lhmm_coupled_destroy(lhmm_coupled_t c);
+
+/* Enqueue n_macro macro steps on `stream`.  With use_graph != 0 the first step
+ * runs eagerly, the second captures one macro step into a CUDA graph, and
+ * every later step replays it (launch overhead of the ~2M+10 kernels of a
+ * step collapses to one graph launch).  Asynchronous. */
+lhmm_status lhmm_coupled_step(lhmm_coupled_t c, int n_macro, int use_graph, void* stream);
+
+/* Device pointers of the exchange buffers: velocity gradients (n_boxes x 9
+ * float) and polymer stresses (n_boxes x 6 double). */
+lhmm_status lhmm_coupled_exchange(lhmm_coupled_t c, float** L_dev, double** stress_dev);
+
+/* Wait for the device and copy the exchange buffers to the host (either
+ * pointer may be NULL).  Synchronous. */
+lhmm_status lhmm_coupled_copy_exchange(lhmm_coupled_t c, float* L_host, double* stress_host);
+
 /* ------------------------------------------------------------------------
  * Allocation-free SPH velocity gradient.  The paper has no counterpart: this
  * entry point exists for callers that may not allocate device memory when

@@ -411,6 +411,13 @@ extern "C" lhmm_status lhmm_sph_recompute_forces(lhmm_sph_t h, const double* str
   return LHMM_OK;
 }
 
+extern "C" lhmm_status lhmm_sph_info(lhmm_sph_t h, int* n, int* n_wall) {
+  if (!h) return LHMM_ERR_ARG;
+  if (n) *n = h->a.n;
+  if (n_wall) *n_wall = h->a.n - h->a.n_fluid;
+  return LHMM_OK;
+}
+
 extern "C" lhmm_status lhmm_sph_get_state(lhmm_sph_t h, float* pos_host, float* vel_host,
                                           float* acc_host, float* density_host) {
   if (!h) return LHMM_ERR_ARG;

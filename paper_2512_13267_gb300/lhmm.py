@@ -92,6 +92,12 @@ def lib():
         L.lhmm_sph_recompute_forces.argtypes = [vp, vp, vp]
         L.lhmm_sph_get_state.argtypes = [vp, _F, _F, _F, _F]
         L.lhmm_sph_velgrad_noalloc.argtypes = [C.POINTER(SphParams), vp, vp, vp, vp]
+        L.lhmm_sph_info.argtypes = [vp, _I, _I]
+        L.lhmm_coupled_create.argtypes = [vp, vp, C.c_int, C.c_int, C.POINTER(vp)]
+        L.lhmm_coupled_destroy.argtypes = [vp]
+        L.lhmm_coupled_step.argtypes = [vp, C.c_int, C.c_int, vp]
+        L.lhmm_coupled_exchange.argtypes = [vp, C.POINTER(vp), C.POINTER(vp)]
+        L.lhmm_coupled_copy_exchange.argtypes = [vp, _F, _D]
         _lib = L
     return _lib
 
@@ -321,3 +327,45 @@ def sph_velgrad_noalloc(params, pos_dev, vel_dev, L_out_dev, stream=None):
     check(lib().lhmm_sph_velgrad_noalloc(C.byref(params), _ptr(pos_dev), _ptr(vel_dev),
                                          _ptr(L_out_dev), _stream_ptr(stream)),
           "lhmm_sph_velgrad_noalloc")
+
+
+class Coupled:
+    """The LHMM macro step over an Sph and a Micro handle (lhmm_coupled_*)."""
+
+    def __init__(self, sph, micro, sph_substeps, micro_steps):
+        h = C.c_void_p()
+        check(lib().lhmm_coupled_create(sph.h, micro.h, int(sph_substeps), int(micro_steps),
+                                        C.byref(h)), "lhmm_coupled_create")
+        self.h = h
+        self.sph, self.micro = sph, micro  # keep the handles alive
+        self.n_boxes = micro.n_boxes
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lhmm_coupled_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n_macro=1, use_graph=True, stream=None):
+        check(lib().lhmm_coupled_step(self.h, int(n_macro), int(bool(use_graph)),
+                                      _stream_ptr(stream)), "lhmm_coupled_step")
+
+    def exchange_ptrs(self):
+        Lp = C.c_void_p()
+        sp = C.c_void_p()
+        check(lib().lhmm_coupled_exchange(self.h, C.byref(Lp), C.byref(sp)),
+              "lhmm_coupled_exchange")
+        return Lp.value, sp.value
+
+    def exchange(self):
+        """Host copies of the exchange buffers (waits for the device)."""
+        L = np.zeros((self.n_boxes, 9), np.float32)
+        st = np.zeros((self.n_boxes, 6), np.float64)
+        check(lib().lhmm_coupled_copy_exchange(self.h, L.ctypes.data_as(_F),
+                                               st.ctypes.data_as(_D)), "lhmm_coupled_copy_exchange")
+        return L, st
