@@ -32,8 +32,9 @@ MICRO_STEPS = 100
 # Algorithmic lane-operations per bead-step (each unique interacting pair
 # once, no rejected candidates); derivation in the design doc.
 PAIRS_PER_BEAD = 2.0 * np.pi / 3.0 * 3.0  # rho (4 pi / 3) rc^3 / 2 at rho = 3
-OPS_PER_PAIR = 136
-OPS_PER_BEAD = 35
+OPS_PER_PAIR = 159   # displacement 6, r^2 + cutoff 4, r and w 3, e.v 7, Philox4x32-10 102,
+#                      Box-Muller 12, force magnitude 9, F on i and j 9, virial 7
+OPS_PER_BEAD = 35    # two half kicks 6, drift 3, cell binning 6, IK kinetic 9, FENE 5, misc 6
 ALGO_OPS_PER_BEAD_STEP = PAIRS_PER_BEAD * OPS_PER_PAIR + OPS_PER_BEAD
 N_SM = 152
 LANES_PER_SM_CLK = 128
