@@ -280,6 +280,54 @@ lhmm_status lhmm_coupled_exchange(lhmm_coupled_t c, float** L_dev, double** stre
 lhmm_status lhmm_coupled_copy_exchange(lhmm_coupled_t c, float* L_host, double* stress_host);
 
 /* ------------------------------------------------------------------------
+ * Learned stress closure (not in the paper; the surrogate layer of this
+ * library).  An ensemble of `members` MLPs in -> hidden x n_hidden -> out with
+ * exact GELU after every hidden layer, BF16 weights on the tensor cores with
+ * FP32 accumulation and FP32 master weights, trained with AdamW (Loshchilov &
+ * Hutter) by this library's own forward and backward kernels.  Inputs are
+ * normalised per feature ((x - mean)/std) and targets scaled per output by
+ * out_scale (lhmm_closure_set_normalization); predictions come back in the
+ * target's units.
+ * ------------------------------------------------------------------------ */
+typedef struct lhmm_closure_s* lhmm_closure_t;
+
+/* members 1..16, hidden a multiple of 32, n_hidden 1..6, out_dim 1..8; weights
+ * He-initialised from `seed`, biases zero.  Synchronous; allocates. */
+lhmm_status lhmm_closure_create(int members, int in_dim, int hidden, int n_hidden, int out_dim,
+                                uint64_t seed, lhmm_closure_t* out);
+lhmm_status lhmm_closure_destroy(lhmm_closure_t c);
+/* host arrays: in_mean, in_std (in_dim), out_scale (out_dim); std, scale > 0 */
+lhmm_status lhmm_closure_set_normalization(lhmm_closure_t c, const float* in_mean_host,
+                                           const float* in_std_host, const float* out_scale_host);
+/* One training step of every member: mean-squared error of the scaled
+ * outputs against T on the member's own batch, gradient, then AdamW
+ * (beta 0.9/0.999, eps 1e-8, decoupled weight decay on weights only) when
+ * lr > 0 (lr = 0: gradient only, see lhmm_closure_get_grad).
+ *   X_dev     device, rows x in_dim float (the sample table)
+ *   T_dev     device, rows x out_dim float (targets, stress units)
+ *   rows_dev  device, members x B int row indices into X/T, or NULL to use
+ *             rows 0..B-1 for every member
+ *   B         batch, a multiple of 32
+ *   loss_dev  device, members float (this step's loss per member) or NULL
+ * Asynchronous; grows the activation workspace on first use of a batch size. */
+lhmm_status lhmm_closure_train_step(lhmm_closure_t c, const float* X_dev, const float* T_dev,
+                                    const int* rows_dev, int B, float lr, float weight_decay,
+                                    float* loss_dev, void* stream);
+/* Ensemble prediction for n inputs: mean_dev n x out_dim (target units) and
+ * spread_dev n = sample standard deviation over members of the output vector
+ * (Euclidean).  Asynchronous. */
+lhmm_status lhmm_closure_infer(lhmm_closure_t c, const float* X_dev, int n, float* mean_dev,
+                               float* spread_dev, void* stream);
+/* Raw scaled outputs of every member (members x n x out_dim, host).  Sync. */
+lhmm_status lhmm_closure_forward(lhmm_closure_t c, const float* X_dev, int n, float* Y_host);
+/* Parameters (and last gradient) of one member as host float arrays in the
+ * layout W_0, b_0, W_1, b_1, ... with W_l row-major (out x in).  Synchronous. */
+lhmm_status lhmm_closure_get_params(lhmm_closure_t c, int member, float* host);
+lhmm_status lhmm_closure_set_params(lhmm_closure_t c, int member, const float* host);
+lhmm_status lhmm_closure_get_grad(lhmm_closure_t c, int member, float* host);
+lhmm_status lhmm_closure_info(lhmm_closure_t c, int64_t* n_params_per_member, int64_t* steps);
+
+/* ------------------------------------------------------------------------
  * Allocation-free SPH velocity gradient.  The paper has no counterpart: this
  * entry point exists for callers that may not allocate device memory when
  * they need the gradients (code inside another framework's memory pool or an

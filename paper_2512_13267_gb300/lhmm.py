@@ -98,6 +98,17 @@ def lib():
         L.lhmm_coupled_step.argtypes = [vp, C.c_int, C.c_int, vp]
         L.lhmm_coupled_exchange.argtypes = [vp, C.POINTER(vp), C.POINTER(vp)]
         L.lhmm_coupled_copy_exchange.argtypes = [vp, _F, _D]
+        L.lhmm_closure_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64,
+                                          C.POINTER(vp)]
+        L.lhmm_closure_destroy.argtypes = [vp]
+        L.lhmm_closure_set_normalization.argtypes = [vp, _F, _F, _F]
+        L.lhmm_closure_train_step.argtypes = [vp, vp, vp, vp, C.c_int, C.c_float, C.c_float, vp, vp]
+        L.lhmm_closure_infer.argtypes = [vp, vp, C.c_int, vp, vp, vp]
+        L.lhmm_closure_forward.argtypes = [vp, vp, C.c_int, _F]
+        L.lhmm_closure_get_params.argtypes = [vp, C.c_int, _F]
+        L.lhmm_closure_set_params.argtypes = [vp, C.c_int, _F]
+        L.lhmm_closure_get_grad.argtypes = [vp, C.c_int, _F]
+        L.lhmm_closure_info.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         _lib = L
     return _lib
 
@@ -369,3 +380,70 @@ class Coupled:
         check(lib().lhmm_coupled_copy_exchange(self.h, L.ctypes.data_as(_F),
                                                st.ctypes.data_as(_D)), "lhmm_coupled_copy_exchange")
         return L, st
+
+
+class Closure:
+    """Ensemble MLP stress closure trained and evaluated on the GPU (lhmm_closure_*)."""
+
+    def __init__(self, members=5, in_dim=67, hidden=256, n_hidden=4, out_dim=3, seed=1):
+        h = C.c_void_p()
+        check(lib().lhmm_closure_create(members, in_dim, hidden, n_hidden, out_dim, seed,
+                                        C.byref(h)), "lhmm_closure_create")
+        self.h = h
+        self.members, self.in_dim, self.out_dim = members, in_dim, out_dim
+        self.dims = [in_dim] + [hidden] * n_hidden + [out_dim]
+        n = C.c_int64()
+        check(lib().lhmm_closure_info(h, C.byref(n), None), "lhmm_closure_info")
+        self.n_params = n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lhmm_closure_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_normalization(self, in_mean, in_std, out_scale):
+        a, pa = _np(in_mean, np.float32)
+        b_, pb = _np(in_std, np.float32)
+        c_, pc = _np(out_scale, np.float32)
+        check(lib().lhmm_closure_set_normalization(self.h, pa, pb, pc),
+              "lhmm_closure_set_normalization")
+
+    def train_step(self, X_dev, T_dev, B, lr, weight_decay=0.0, rows_dev=None, loss_dev=None,
+                   stream=None):
+        check(lib().lhmm_closure_train_step(self.h, _ptr(X_dev), _ptr(T_dev), _ptr(rows_dev),
+                                            int(B), float(lr), float(weight_decay),
+                                            _ptr(loss_dev), _stream_ptr(stream)),
+              "lhmm_closure_train_step")
+
+    def infer(self, X_dev, mean_dev, spread_dev, stream=None):
+        check(lib().lhmm_closure_infer(self.h, _ptr(X_dev), int(X_dev.shape[0]), _ptr(mean_dev),
+                                       _ptr(spread_dev), _stream_ptr(stream)), "lhmm_closure_infer")
+
+    def forward_members(self, X_dev):
+        n = int(X_dev.shape[0])
+        Y = np.zeros((self.members, n, self.out_dim), np.float32)
+        check(lib().lhmm_closure_forward(self.h, _ptr(X_dev), n, Y.ctypes.data_as(_F)),
+              "lhmm_closure_forward")
+        return Y
+
+    def get_params(self, member=0):
+        p = np.zeros(self.n_params, np.float32)
+        check(lib().lhmm_closure_get_params(self.h, int(member), p.ctypes.data_as(_F)),
+              "lhmm_closure_get_params")
+        return p
+
+    def set_params(self, member, params):
+        p, pp = _np(params, np.float32)
+        check(lib().lhmm_closure_set_params(self.h, int(member), pp), "lhmm_closure_set_params")
+
+    def get_grad(self, member=0):
+        g = np.zeros(self.n_params, np.float32)
+        check(lib().lhmm_closure_get_grad(self.h, int(member), g.ctypes.data_as(_F)),
+              "lhmm_closure_get_grad")
+        return g
