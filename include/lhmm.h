@@ -127,6 +127,16 @@ lhmm_status lhmm_micro_advance(lhmm_micro_t h, const float* L_dev, const int* bo
                                int n_active, int n_steps, double* stress_dev,
                                double* stress_sq_dev, void* stream);
 
+/* The same over a box list whose length is known only on the device (e.g. the
+ * output of a gate): the boxes box_idx_dev[0 .. min(*n_active_dev, max_active))
+ * are advanced by a persistent launch whose blocks take list items from a
+ * device counter.  max_active <= n_boxes bounds the list.  Asynchronous;
+ * capturable in a CUDA graph. */
+lhmm_status lhmm_micro_advance_dev_count(lhmm_micro_t h, const float* L_dev,
+                                         const int* box_idx_dev, const int* n_active_dev,
+                                         int max_active, int n_steps, double* stress_dev,
+                                         double* stress_sq_dev, void* stream);
+
 /* The same over host buffers: copies L_host (n_boxes x 9) in, advances all
  * boxes, copies stress (n_boxes x 6) and optionally stress_sq back, and waits
  * for the stream.  Synchronous.  Uses staging buffers owned by the handle. */
@@ -326,6 +336,32 @@ lhmm_status lhmm_closure_get_params(lhmm_closure_t c, int member, float* host);
 lhmm_status lhmm_closure_set_params(lhmm_closure_t c, int member, const float* host);
 lhmm_status lhmm_closure_get_grad(lhmm_closure_t c, int member, float* host);
 lhmm_status lhmm_closure_info(lhmm_closure_t c, int64_t* n_params_per_member, int64_t* steps);
+
+/* ------------------------------------------------------------------------
+ * Surrogate-gated macro step (not in the paper).  With a closure attached,
+ * every macro step pushes each particle's gradient (Lxx, Lxy, Lyx, Lyy) into a
+ * 16-deep ring and builds the closure input [16 past gradients oldest first,
+ * pi_xx, pi_xy, pi_yy] (67 floats).  With the gate enabled, a macro step then
+ * runs the ensemble; a particle whose ensemble spread exceeds
+ * threshold x max(|predicted in-plane stress tensor| (Frobenius), stress_floor)
+ * -- or every audit_every-th trusted particle, round robin --
+ * runs its DPD box (persistent launch over the device-built list); the others
+ * keep their boxes frozen and take pi += predicted increment.  Audited boxes
+ * measure the surrogate's live error against DPD.
+ * ------------------------------------------------------------------------ */
+/* Attach a closure (67 inputs, 3 outputs: increments of pi_xx, pi_xy, pi_yy);
+ * the gate starts disabled.  Synchronous; allocates the gate buffers. */
+lhmm_status lhmm_coupled_set_closure(lhmm_coupled_t c, lhmm_closure_t closure, float threshold,
+                                     float stress_floor, int audit_every);
+lhmm_status lhmm_coupled_enable_gate(lhmm_coupled_t c, int enabled);
+/* Counters since the closure was attached: gated macro steps, boxes advanced
+ * by DPD in them, audited boxes, and over the audited boxes the summed squared
+ * error of the predicted increment and the summed squared DPD increment.
+ * Synchronous. */
+lhmm_status lhmm_coupled_gate_stats(lhmm_coupled_t c, int64_t* gated_steps, int64_t* dpd_boxes,
+                                    int64_t* audited_boxes, double* audit_err2, double* audit_ref2);
+/* The closure inputs of the last macro step (n_boxes x 67, host).  Sync. */
+lhmm_status lhmm_coupled_closure_inputs(lhmm_coupled_t c, float* X_host);
 
 /* ------------------------------------------------------------------------
  * Allocation-free SPH velocity gradient.  The paper has no counterpart: this

@@ -10,6 +10,29 @@
 
 #include "lhmm_common.cuh"
 
+// Surrogate gate state (the learned closure is not in the paper).
+constexpr int kHist = 16;          // velocity-gradient samples in the closure input
+constexpr int kFeat = 4 * kHist + 3;
+
+struct GateState {
+  lhmm_closure_t closure = nullptr;
+  float threshold = 0.02f;  // relative ensemble spread above which a box runs DPD
+  float floor = 1e-3f;      // stress scale floor of the relative spread
+  int audit_every = 50;     // every audit_every-th trusted box (round robin) runs DPD anyway
+  int enabled = 0;
+  float* hist = nullptr;    // n x kHist x 4 ring of (Lxx, Lxy, Lyx, Lyy)
+  float* X = nullptr;       // n x kFeat closure inputs
+  float* mean = nullptr;    // n x 3 predicted increments (xx, xy, yy)
+  float* spread = nullptr;  // n
+  int* active = nullptr;    // n box list for DPD
+  int* n_active = nullptr;  // device count of the list
+  long long* counters = nullptr;  // [0] gated steps, [1] DPD boxes, [2] audited boxes, [3] ring head
+  double* audit = nullptr;  // [0] sum |pred - dpd|^2, [1] sum |dpd|^2 over audited boxes
+  unsigned char* audited = nullptr;  // n
+  float* pred = nullptr;    // n x 3 prediction of audited boxes
+  float* before = nullptr;  // n x 3 stress before the step of audited boxes
+};
+
 struct lhmm_coupled_s {
   lhmm_sph_t sph = nullptr;
   lhmm_micro_t micro = nullptr;
@@ -17,27 +40,153 @@ struct lhmm_coupled_s {
   float* L_d = nullptr;         // n_boxes x 9, SPH -> micro
   double* stress_d = nullptr;   // n_boxes x 6, micro -> SPH
   cudaStream_t capture_stream = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  long long steps_done = 0;
+  cudaGraph_t graph[2] = {nullptr, nullptr};      // plain, gated
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  long long steps_done = 0, mode_steps[2] = {0, 0};
+  GateState gate;
 };
 
 namespace {
 
-lhmm_status enqueue_macro_step(lhmm_coupled_s* c, cudaStream_t s) {
+// push this step's gradient into the ring and build the closure input
+// [L(t-15) .. L(t) as (Lxx, Lxy, Lyx, Lyy), pi_xx, pi_xy, pi_yy]
+__global__ void gate_features(const float* L, const double* stress, int n, float* hist,
+                              const long long* counters, float* X) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  const int head = static_cast<int>(counters[3] % kHist);
+  float* h = hist + static_cast<long long>(I) * kHist * 4;
+  const float* l = L + 9 * static_cast<long long>(I);
+  h[4 * head + 0] = l[0];
+  h[4 * head + 1] = l[1];
+  h[4 * head + 2] = l[3];
+  h[4 * head + 3] = l[4];
+  float* x = X + static_cast<long long>(I) * kFeat;
+  for (int k = 0; k < kHist; ++k) {
+    const int src = (head + 1 + k) % kHist;  // oldest first
+    for (int q = 0; q < 4; ++q) x[4 * k + q] = h[4 * src + q];
+  }
+  const double* s = stress + 6 * static_cast<long long>(I);
+  x[4 * kHist + 0] = static_cast<float>(s[0]);
+  x[4 * kHist + 1] = static_cast<float>(s[3]);
+  x[4 * kHist + 2] = static_cast<float>(s[1]);
+}
+
+__global__ void advance_ring(long long* counters) { counters[3] += 1; }
+
+// trust test and compaction; trusted boxes take the predicted increment,
+// the others (and an audit share of the trusted ones) go to the DPD list
+__global__ void gate_select(const float* mean, const float* spread, double* stress, int n,
+                            float thr, float floor_, int audit_every, long long* counters,
+                            int* active, int* n_active, unsigned char* audited, float* pred,
+                            float* before) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  double* s = stress + 6 * static_cast<long long>(I);
+  const float dxx = mean[3 * I], dxy = mean[3 * I + 1], dyy = mean[3 * I + 2];
+  // scale: magnitude (Frobenius) of the predicted in-plane stress tensor
+  const float pxx = static_cast<float>(s[0]) + dxx, pxy = static_cast<float>(s[3]) + dxy,
+              pyy = static_cast<float>(s[1]) + dyy;
+  const float scale = fmaxf(sqrtf(pxx * pxx + 2.f * pxy * pxy + pyy * pyy), floor_);
+  const bool trust = spread[I] <= thr * scale;
+  const long long step = counters[0];
+  const bool audit = trust && audit_every > 0 && ((I + step) % audit_every) == 0;
+  if (!trust || audit) {
+    active[atomicAdd(n_active, 1)] = I;
+    if (audit) {
+      audited[I] = 1;
+      pred[3 * I] = dxx;
+      pred[3 * I + 1] = dxy;
+      pred[3 * I + 2] = dyy;
+      before[3 * I] = static_cast<float>(s[0]);
+      before[3 * I + 1] = static_cast<float>(s[3]);
+      before[3 * I + 2] = static_cast<float>(s[1]);
+    }
+  } else {
+    s[0] += dxx;
+    s[3] += dxy;
+    s[1] += dyy;
+  }
+}
+
+__global__ void gate_tally(long long* counters, const int* n_active) {
+  counters[0] += 1;
+  counters[1] += *n_active;
+}
+
+__global__ void gate_audit(const double* stress, int n, unsigned char* audited, const float* pred,
+                           const float* before, long long* counters, double* audit) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n || !audited[I]) return;
+  audited[I] = 0;
+  const double* s = stress + 6 * static_cast<long long>(I);
+  const double a0 = s[0] - before[3 * I], a1 = s[3] - before[3 * I + 1], a2 = s[1] - before[3 * I + 2];
+  const double e0 = pred[3 * I] - a0, e1 = pred[3 * I + 1] - a1, e2 = pred[3 * I + 2] - a2;
+  atomicAdd(&audit[0], e0 * e0 + e1 * e1 + e2 * e2);
+  atomicAdd(&audit[1], a0 * a0 + a1 * a1 + a2 * a2);
+  atomicAdd(reinterpret_cast<unsigned long long*>(&counters[2]), 1ull);
+}
+
+lhmm_status enqueue_macro_step(lhmm_coupled_s* c, cudaStream_t s, bool gated) {
   lhmm_status st = lhmm_sph_step(c->sph, c->stress_d, c->sph_substeps, c->L_d, s);
   if (st != LHMM_OK) return st;
-  return lhmm_micro_advance(c->micro, c->L_d, nullptr, c->n_boxes, c->micro_steps, c->stress_d,
-                            nullptr, s);
+  GateState& g = c->gate;
+  const int n = c->n_boxes, T = 128, G = (n + T - 1) / T;
+  if (g.closure) {
+    gate_features<<<G, T, 0, s>>>(c->L_d, c->stress_d, n, g.hist, g.counters, g.X);
+    advance_ring<<<1, 1, 0, s>>>(g.counters);
+    LHMM_CK(cudaGetLastError());
+  }
+  if (!gated) {
+    return lhmm_micro_advance(c->micro, c->L_d, nullptr, n, c->micro_steps, c->stress_d, nullptr, s);
+  }
+  st = lhmm_closure_infer(g.closure, g.X, n, g.mean, g.spread, s);
+  if (st != LHMM_OK) return st;
+  LHMM_CK(cudaMemsetAsync(g.n_active, 0, sizeof(int), s));
+  gate_select<<<G, T, 0, s>>>(g.mean, g.spread, c->stress_d, n, g.threshold, g.floor, g.audit_every,
+                              g.counters, g.active, g.n_active, g.audited, g.pred, g.before);
+  gate_tally<<<1, 1, 0, s>>>(g.counters, g.n_active);
+  LHMM_CK(cudaGetLastError());
+  st = lhmm_micro_advance_dev_count(c->micro, c->L_d, g.active, g.n_active, n, c->micro_steps,
+                                    c->stress_d, nullptr, s);
+  if (st != LHMM_OK) return st;
+  gate_audit<<<G, T, 0, s>>>(c->stress_d, n, g.audited, g.pred, g.before, g.counters, g.audit);
+  LHMM_CK(cudaGetLastError());
+  return LHMM_OK;
+}
+
+void free_gate(GateState& g) {
+  cudaFree(g.hist);
+  cudaFree(g.X);
+  cudaFree(g.mean);
+  cudaFree(g.spread);
+  cudaFree(g.active);
+  cudaFree(g.n_active);
+  cudaFree(g.counters);
+  cudaFree(g.audit);
+  cudaFree(g.audited);
+  cudaFree(g.pred);
+  cudaFree(g.before);
+  g = GateState();
+}
+
+void drop_graphs(lhmm_coupled_s* c) {
+  for (int m = 0; m < 2; ++m) {
+    if (c->exec[m]) cudaGraphExecDestroy(c->exec[m]);
+    if (c->graph[m]) cudaGraphDestroy(c->graph[m]);
+    c->exec[m] = nullptr;
+    c->graph[m] = nullptr;
+    c->mode_steps[m] = 0;
+  }
 }
 
 void free_coupled(lhmm_coupled_s* c) {
   if (!c) return;
-  if (c->exec) cudaGraphExecDestroy(c->exec);
-  if (c->graph) cudaGraphDestroy(c->graph);
+  drop_graphs(c);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
   cudaFree(c->L_d);
   cudaFree(c->stress_d);
+  free_gate(c->gate);
   delete c;
 }
 
@@ -86,16 +235,19 @@ extern "C" lhmm_status lhmm_coupled_step(lhmm_coupled_t c, int n_macro, int use_
                                          void* stream) {
   if (!c || n_macro < 0) return LHMM_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool gated = c->gate.closure && c->gate.enabled;
+  const int mode = gated ? 1 : 0;
   for (int k = 0; k < n_macro; ++k) {
-    if (!use_graph || c->steps_done == 0) {
-      // eager (the first step also sets kernel attributes before any capture)
-      lhmm_status st = enqueue_macro_step(c, s);
+    if (!use_graph || c->mode_steps[mode] == 0) {
+      // eager (the first step of a mode also sets kernel attributes and grows
+      // workspaces before any capture)
+      lhmm_status st = enqueue_macro_step(c, s, gated);
       if (st != LHMM_OK) return st;
     } else {
-      if (!c->exec) {
+      if (!c->exec[mode]) {
         LHMM_CK(cudaStreamSynchronize(s));
         LHMM_CK(cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
-        lhmm_status st = enqueue_macro_step(c, c->capture_stream);
+        lhmm_status st = enqueue_macro_step(c, c->capture_stream, gated);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(c->capture_stream, &g);
         if (st != LHMM_OK) {
@@ -103,17 +255,86 @@ extern "C" lhmm_status lhmm_coupled_step(lhmm_coupled_t c, int n_macro, int use_
           return st;
         }
         if (e != cudaSuccess) return lhmm_cuda_error(e);
-        c->graph = g;
-        e = cudaGraphInstantiate(&c->exec, g, 0);
+        c->graph[mode] = g;
+        e = cudaGraphInstantiate(&c->exec[mode], g, 0);
         if (e != cudaSuccess) {
-          c->exec = nullptr;
+          c->exec[mode] = nullptr;
           return lhmm_cuda_error(e);
         }
       }
-      LHMM_CK(cudaGraphLaunch(c->exec, s));
+      LHMM_CK(cudaGraphLaunch(c->exec[mode], s));
     }
+    ++c->mode_steps[mode];
     ++c->steps_done;
   }
+  return LHMM_OK;
+}
+
+extern "C" lhmm_status lhmm_coupled_set_closure(lhmm_coupled_t c, lhmm_closure_t closure,
+                                                float threshold, float stress_floor,
+                                                int audit_every) {
+  if (!c || !closure || !(threshold >= 0.f) || !(stress_floor > 0.f) || audit_every < 0)
+    return LHMM_ERR_ARG;
+  LHMM_CK(cudaDeviceSynchronize());
+  drop_graphs(c);
+  free_gate(c->gate);
+  GateState& g = c->gate;
+  const size_t n = static_cast<size_t>(c->n_boxes > 0 ? c->n_boxes : 1);
+  cudaError_t e;
+  if ((e = cudaMalloc(&g.hist, sizeof(float) * n * kHist * 4)) != cudaSuccess ||
+      (e = cudaMalloc(&g.X, sizeof(float) * n * kFeat)) != cudaSuccess ||
+      (e = cudaMalloc(&g.mean, sizeof(float) * n * 3)) != cudaSuccess ||
+      (e = cudaMalloc(&g.spread, sizeof(float) * n)) != cudaSuccess ||
+      (e = cudaMalloc(&g.active, sizeof(int) * n)) != cudaSuccess ||
+      (e = cudaMalloc(&g.n_active, sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&g.counters, sizeof(long long) * 4)) != cudaSuccess ||
+      (e = cudaMalloc(&g.audit, sizeof(double) * 2)) != cudaSuccess ||
+      (e = cudaMalloc(&g.audited, n)) != cudaSuccess ||
+      (e = cudaMalloc(&g.pred, sizeof(float) * n * 3)) != cudaSuccess ||
+      (e = cudaMalloc(&g.before, sizeof(float) * n * 3)) != cudaSuccess ||
+      (e = cudaMemset(g.hist, 0, sizeof(float) * n * kHist * 4)) != cudaSuccess ||
+      (e = cudaMemset(g.counters, 0, sizeof(long long) * 4)) != cudaSuccess ||
+      (e = cudaMemset(g.audit, 0, sizeof(double) * 2)) != cudaSuccess ||
+      (e = cudaMemset(g.audited, 0, n)) != cudaSuccess ||
+      (e = cudaMemset(g.n_active, 0, sizeof(int))) != cudaSuccess) {
+    free_gate(g);
+    return lhmm_cuda_error(e);
+  }
+  g.closure = closure;
+  g.threshold = threshold;
+  g.floor = stress_floor;
+  g.audit_every = audit_every;
+  g.enabled = 0;
+  return LHMM_OK;
+}
+
+extern "C" lhmm_status lhmm_coupled_enable_gate(lhmm_coupled_t c, int enabled) {
+  if (!c || !c->gate.closure) return LHMM_ERR_ARG;
+  c->gate.enabled = enabled ? 1 : 0;
+  return LHMM_OK;
+}
+
+extern "C" lhmm_status lhmm_coupled_gate_stats(lhmm_coupled_t c, int64_t* gated_steps,
+                                               int64_t* dpd_boxes, int64_t* audited_boxes,
+                                               double* audit_err2, double* audit_ref2) {
+  if (!c || !c->gate.closure) return LHMM_ERR_ARG;
+  LHMM_CK(cudaDeviceSynchronize());
+  long long cnt[4];
+  double au[2];
+  LHMM_CK(cudaMemcpy(cnt, c->gate.counters, sizeof(cnt), cudaMemcpyDeviceToHost));
+  LHMM_CK(cudaMemcpy(au, c->gate.audit, sizeof(au), cudaMemcpyDeviceToHost));
+  if (gated_steps) *gated_steps = cnt[0];
+  if (dpd_boxes) *dpd_boxes = cnt[1];
+  if (audited_boxes) *audited_boxes = cnt[2];
+  if (audit_err2) *audit_err2 = au[0];
+  if (audit_ref2) *audit_ref2 = au[1];
+  return LHMM_OK;
+}
+
+extern "C" lhmm_status lhmm_coupled_closure_inputs(lhmm_coupled_t c, float* X_host) {
+  if (!c || !c->gate.closure || !X_host) return LHMM_ERR_ARG;
+  LHMM_CK(cudaDeviceSynchronize());
+  LHMM_CK(cudaMemcpy(X_host, c->gate.X, sizeof(float) * c->n_boxes * kFeat, cudaMemcpyDeviceToHost));
   return LHMM_OK;
 }
 

@@ -74,6 +74,9 @@ struct MicroArgs {
   int flow, dpd_on_bonded, chain_len;
   int max_beads, max_cells;
   int n_boxes;
+  int* work_counter;         // persistent mode: next work item (NULL: one block per item)
+  const int* n_items_dev;    // persistent mode: device-side item count
+  int max_items;             // persistent mode: capacity of the item list
 };
 
 constexpr int kRedFloats = 192;  // 6 x 32 warps, also scan scratch
@@ -153,15 +156,14 @@ __device__ __forceinline__ void cell_coords(int c, int nx, int nxy, float inx, f
   cx = rem - cy * nx;
 }
 
-template <int T, int MINB>
-__global__ void __launch_bounds__(T, MINB) micro_kernel(const MicroArgs A) {
+template <int T>
+__device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ BoxInfo sB;
   __shared__ float sL[9];
   constexpr int NW = T / 32;
   constexpr unsigned FULL = 0xffffffffu;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int bid = A.list[blockIdx.x];
   if (bid < 0 || bid >= A.n_boxes) return;  // whole block leaves together
   if (tid == 0) sB = A.boxes[bid];
   if (tid < 9) sL[tid] = A.lambda_star * A.L[9 * bid + tid];
@@ -682,6 +684,31 @@ __global__ void __launch_bounds__(T, MINB) micro_kernel(const MicroArgs A) {
   }
 }
 
+
+// One block per listed box.
+template <int T, int MINB>
+__global__ void __launch_bounds__(T, MINB) micro_kernel(const MicroArgs A) {
+  micro_box<T>(A, A.list[blockIdx.x]);
+}
+
+// Persistent form: a fixed grid whose blocks pull item indices from a device
+// counter up to a device-side count, so the set of boxes can be chosen on the
+// device (e.g. by a gate inside a CUDA graph).
+template <int T, int MINB>
+__global__ void __launch_bounds__(T, MINB) micro_kernel_persistent(const MicroArgs A) {
+  __shared__ int s_item;
+  const int limit = min(*A.n_items_dev, A.max_items);
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(A.work_counter, 1);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= limit) return;
+    micro_box<T>(A, A.list[item]);
+    __syncthreads();
+  }
+}
+
 // Launch variants: threads per block and the resident blocks per SM that
 // the register allocation must allow (64 registers/thread for 2048/SM).
 struct Variant {
@@ -692,15 +719,22 @@ constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 template <int T, int MINB>
 cudaError_t launch_micro(const MicroArgs& a, int grid, size_t smem, cudaStream_t s) {
-  static size_t attr_bytes = 0;
-  if (smem > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(micro_kernel<T, MINB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+  static size_t attr_bytes = 0, attr_bytes_p = 0;
+  const bool persistent = a.work_counter != nullptr;
+  size_t& done = persistent ? attr_bytes_p : attr_bytes;
+  if (smem > done) {
+    cudaError_t e = persistent
+                        ? cudaFuncSetAttribute(micro_kernel_persistent<T, MINB>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               static_cast<int>(smem))
+                        : cudaFuncSetAttribute(micro_kernel<T, MINB>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    attr_bytes = smem;
+    done = smem;
   }
-  micro_kernel<T, MINB><<<grid, T, smem, s>>>(a);
+  if (persistent) micro_kernel_persistent<T, MINB><<<grid, T, smem, s>>>(a);
+  else micro_kernel<T, MINB><<<grid, T, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -742,6 +776,7 @@ struct lhmm_micro_s {
   cudaStream_t stream = nullptr;
   std::vector<SizeClass> classes;
   cudaEvent_t fork = nullptr;
+  int* work_counter = nullptr;  // persistent-mode item counter
   int subset_variant = 1;  // single launch over a device-side box list
 };
 
@@ -814,6 +849,7 @@ void free_micro(lhmm_micro_t h) {
     if (c.done) cudaEventDestroy(c.done);
   }
   if (h->fork) cudaEventDestroy(h->fork);
+  cudaFree(h->work_counter);
   delete h;
 }
 
@@ -992,7 +1028,8 @@ extern "C" lhmm_status lhmm_micro_create(const lhmm_dpd_params* params,
       (e = cudaMalloc(&h->L_stage, sizeof(float) * 9 * nbx)) != cudaSuccess ||
       (e = cudaMalloc(&h->st_stage, sizeof(double) * 6 * nbx)) != cudaSuccess ||
       (e = cudaMalloc(&h->sq_stage, sizeof(double) * 6 * nbx)) != cudaSuccess ||
-      (e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming)) != cudaSuccess)
+      (e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaMalloc(&h->work_counter, sizeof(int))) != cudaSuccess)
     return fail(lhmm_cuda_error(e));
   for (auto& c : h->classes) {
     if ((e = cudaMalloc(&c.boxes_d, sizeof(int) * c.boxes.size())) != cudaSuccess ||
@@ -1067,6 +1104,34 @@ extern "C" lhmm_status lhmm_micro_advance(lhmm_micro_t h, const float* L_dev,
   } else {
     LHMM_CK(launch_classes(h, a, s));
   }
+  return LHMM_OK;
+}
+
+extern "C" lhmm_status lhmm_micro_advance_dev_count(lhmm_micro_t h, const float* L_dev,
+                                                    const int* box_idx_dev,
+                                                    const int* n_active_dev, int max_active,
+                                                    int n_steps, double* stress_dev,
+                                                    double* stress_sq_dev, void* stream) {
+  if (!h || !box_idx_dev || !n_active_dev || max_active < 0 || n_steps < 0) return LHMM_ERR_ARG;
+  if (max_active > h->n_boxes) return LHMM_ERR_ARG;
+  if (n_steps == 0 || max_active == 0) return LHMM_OK;
+  if (!L_dev || !stress_dev) return LHMM_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  MicroArgs a = make_args(h);
+  a.L = L_dev;
+  a.stress = stress_dev;
+  a.stress_sq = stress_sq_dev;
+  a.n_steps = n_steps;
+  a.init_forces = 0;
+  a.work_counter = h->work_counter;
+  a.n_items_dev = n_active_dev;
+  a.max_items = max_active;
+  int dev = 0, n_sm = 0;
+  LHMM_CK(cudaGetDevice(&dev));
+  LHMM_CK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = std::min(max_active, 2 * n_sm);
+  LHMM_CK(cudaMemsetAsync(h->work_counter, 0, sizeof(int), s));
+  LHMM_CK(launch_subset(h, a, box_idx_dev, grid, s));
   return LHMM_OK;
 }
 

@@ -98,6 +98,12 @@ def lib():
         L.lhmm_coupled_step.argtypes = [vp, C.c_int, C.c_int, vp]
         L.lhmm_coupled_exchange.argtypes = [vp, C.POINTER(vp), C.POINTER(vp)]
         L.lhmm_coupled_copy_exchange.argtypes = [vp, _F, _D]
+        L.lhmm_coupled_set_closure.argtypes = [vp, vp, C.c_float, C.c_float, C.c_int]
+        L.lhmm_coupled_enable_gate.argtypes = [vp, C.c_int]
+        L.lhmm_coupled_gate_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                              C.POINTER(C.c_int64), _D, _D]
+        L.lhmm_coupled_closure_inputs.argtypes = [vp, _F]
+        L.lhmm_micro_advance_dev_count.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int, vp, vp, vp]
         L.lhmm_closure_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64,
                                           C.POINTER(vp)]
         L.lhmm_closure_destroy.argtypes = [vp]
@@ -372,6 +378,29 @@ class Coupled:
         check(lib().lhmm_coupled_exchange(self.h, C.byref(Lp), C.byref(sp)),
               "lhmm_coupled_exchange")
         return Lp.value, sp.value
+
+    def set_closure(self, closure, threshold=0.02, stress_floor=1e-3, audit_every=50):
+        check(lib().lhmm_coupled_set_closure(self.h, closure.h, float(threshold),
+                                             float(stress_floor), int(audit_every)),
+              "lhmm_coupled_set_closure")
+        self.closure = closure
+
+    def enable_gate(self, on=True):
+        check(lib().lhmm_coupled_enable_gate(self.h, int(bool(on))), "lhmm_coupled_enable_gate")
+
+    def gate_stats(self):
+        a, b_, c_ = C.c_int64(), C.c_int64(), C.c_int64()
+        e, r = C.c_double(), C.c_double()
+        check(lib().lhmm_coupled_gate_stats(self.h, C.byref(a), C.byref(b_), C.byref(c_),
+                                            C.byref(e), C.byref(r)), "lhmm_coupled_gate_stats")
+        return dict(gated_steps=a.value, dpd_boxes=b_.value, audited=c_.value,
+                    audit_err2=e.value, audit_ref2=r.value)
+
+    def closure_inputs(self):
+        X = np.zeros((self.n_boxes, 67), np.float32)
+        check(lib().lhmm_coupled_closure_inputs(self.h, X.ctypes.data_as(_F)),
+              "lhmm_coupled_closure_inputs")
+        return X
 
     def exchange(self):
         """Host copies of the exchange buffers (waits for the device)."""

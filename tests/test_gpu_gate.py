@@ -1,0 +1,100 @@
+"""The surrogate gate inside the coupled macro step: closure inputs, the
+all-DPD and all-surrogate limits, counters."""
+import numpy as np
+import pytest
+
+from paper_2512_13267_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def _system(seed=7, nx=8, ny=8, Ly=1.0):
+    from paper_2512_13267_gb300 import lhmm as lh
+    dh = Ly / ny
+    Lx = nx * dh
+    pos = S.sph_lattice(nx, ny, Lx, Ly, seed=seed, jitter=0.1).astype(np.float32)
+    vel = np.random.default_rng(seed).normal(scale=0.05, size=pos.shape).astype(np.float32)
+    n = pos.shape[0]
+    batch = S.make_batch(np.full(n, 4.0), np.zeros((n, 9), np.float32), seed, flow="afbc")
+    sp = lh.sph_params(n, 0, Lx=Lx, Ly=Ly, h=3 * dh, mass=dh * dh, rho0=1.0, c=2.0,
+                       theta_pb=0.1, eta_s=0.2, dt=0.01, body_force=(0.3, 0.0),
+                       body_mode=lh.SPH_BODY_REVERSE_POISEUILLE)
+    sph = lh.Sph(sp, pos, vel)
+    micro = lh.Micro.from_batch(lh.dpd_params(flow="afbc", seed=5, alpha=0.05), batch)
+    cpl = lh.Coupled(sph, micro, 4, 6)
+    clo = lh.Closure(members=5, in_dim=67, hidden=256, n_hidden=4, out_dim=3, seed=2)
+    clo.set_normalization(np.zeros(67), np.ones(67), np.full(3, 1e-3))
+    return cpl, clo
+
+
+def test_closure_inputs_hold_gradient_history_and_stress():
+    cpl, clo = _system()
+    cpl.set_closure(clo, threshold=0.02)
+    Ls, Ss = [], []
+    for _ in range(18):
+        _, st_before = cpl.exchange()
+        cpl.step(1, use_graph=True)
+        L, _ = cpl.exchange()
+        Ls.append(L[:, [0, 1, 3, 4]].copy())
+        Ss.append(st_before[:, [0, 3, 1]].astype(np.float32))
+    X = cpl.closure_inputs()
+    hist = np.stack(Ls[-16:], axis=1).reshape(X.shape[0], 64)
+    assert np.array_equal(X[:, :64], hist)
+    assert np.array_equal(X[:, 64:67], Ss[-1])
+
+
+def test_zero_threshold_gate_equals_plain_step():
+    a, ca = _system(seed=9)
+    b, cb = _system(seed=9)
+    a.set_closure(ca, threshold=0.0)
+    b.set_closure(cb, threshold=0.0)
+    a.step(3, use_graph=True)
+    b.step(3, use_graph=True)
+    b.enable_gate(True)
+    a.step(3, use_graph=True)
+    b.step(3, use_graph=True)  # eager, capture, replay of the gated graph
+    La, sa = a.exchange()
+    Lb, sb = b.exchange()
+    assert np.array_equal(La, Lb) and np.array_equal(sa, sb)
+    st = b.gate_stats()
+    assert st["gated_steps"] == 3 and st["dpd_boxes"] == 3 * b.n_boxes
+
+
+def test_open_gate_freezes_boxes_and_applies_prediction():
+    cpl, clo = _system(seed=11)
+    cpl.set_closure(clo, threshold=1e30, audit_every=0)
+    cpl.step(17, use_graph=True)
+    steps_before = [cpl.micro.get_state(b)[3] for b in range(cpl.n_boxes)]
+    _, st0 = cpl.exchange()
+    cpl.enable_gate(True)
+    cpl.step(1, use_graph=False)
+    X = cpl.closure_inputs()
+    _, st1 = cpl.exchange()
+    assert [cpl.micro.get_state(b)[3] for b in range(cpl.n_boxes)] == steps_before
+    mean = torch.zeros((cpl.n_boxes, 3), dtype=torch.float32, device="cuda")
+    spread = torch.zeros(cpl.n_boxes, dtype=torch.float32, device="cuda")
+    clo.infer(torch.from_numpy(X).cuda(), mean, spread)
+    d = st1[:, [0, 3, 1]] - st0[:, [0, 3, 1]]
+    assert np.allclose(d, mean.cpu().numpy(), rtol=1e-5, atol=1e-7)
+    assert np.array_equal(st1[:, [2, 4, 5]], st0[:, [2, 4, 5]])
+    assert cpl.gate_stats()["dpd_boxes"] == 0
+
+
+def test_audit_share_runs_dpd_and_measures_error():
+    cpl, clo = _system(seed=13)
+    cpl.set_closure(clo, threshold=1e30, audit_every=4)
+    cpl.step(17, use_graph=True)
+    cpl.enable_gate(True)
+    cpl.step(4, use_graph=True)
+    st = cpl.gate_stats()
+    assert st["gated_steps"] == 4
+    assert st["dpd_boxes"] == st["audited"] == 4 * cpl.n_boxes // 4
+    assert st["audit_ref2"] > 0 and st["audit_err2"] > 0
