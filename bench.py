@@ -153,15 +153,13 @@ def macro_step_rate(steps=10, warmup=2):
     M SPH substeps from the CFL rule), graph-captured macro steps."""
     import torch
     from paper_2512_13267_gb300 import lhmm, synth
-    U_o, c_fac, eta_s, alpha, k_micro, dt_dpd = 1.0, 10.0, 0.5, 0.01, 50, 0.01
+    U_o, c_fac, eta_s, alpha, k_micro, dt_dpd = 0.25, 10.0, 0.1, 0.01, 50, 0.01
     sph_cfg, batch = synth.coupled_channel(U_o=U_o, c_factor=c_fac, eta_s=eta_s,
-                                           eta_tot=eta_s + 0.01)
-    delta_t = k_micro * dt_dpd                    # exchange interval (lambda* = 1)
-    dt_cfl = 0.25 * sph_cfg["h"] / (1.5 * U_o + sph_cfg["c"])
-    M = int(np.ceil(delta_t / dt_cfl))
+                                           delta_t=k_micro * dt_dpd)
+    M = sph_cfg["substeps"]
     sp = lhmm.sph_params(sph_cfg["pos"].shape[0], 0, Lx=sph_cfg["Lx"], Ly=sph_cfg["Ly"],
                          h=sph_cfg["h"], mass=sph_cfg["mass"], rho0=1.0, c=sph_cfg["c"],
-                         theta_pb=0.1, eta_s=eta_s, dt=delta_t / M,
+                         theta_pb=0.1, eta_s=eta_s, dt=sph_cfg["dt"],
                          body_force=(sph_cfg["body_force"], 0.0),
                          body_mode=lhmm.SPH_BODY_REVERSE_POISEUILLE)
     sph = lhmm.Sph(sp, sph_cfg["pos"], sph_cfg["vel"])
@@ -188,7 +186,7 @@ def macro_step_rate(steps=10, warmup=2):
            "bead_steps_per_s": batch.total_beads * k_micro * steps / (ms / 1e3),
            "cuda_graph": True, "device_status": lhmm.status_string(status),
            "workload": "coupled reverse-Poiseuille channel 64x32 SPH (Ly=4, h=3dh, Wendland, "
-                       "c=10 U_o) x 1500-bead AFBC boxes, k'=50, M=%d" % M}
+                       "c=10 U_o, U_o=0.25, eta_s=0.1) x 1500-bead AFBC boxes, k'=50, M=%d" % M}
     cpl.close()
     micro.close()
     sph.close()

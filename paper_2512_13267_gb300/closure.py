@@ -83,3 +83,96 @@ def binned_profiles(y, stress6, Ly, nbins=16):
 
 def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def _channel(seed, alpha, U_o, c_factor, eta_s, k_micro, dt_dpd, members, closure_seed):
+    from . import synth
+    sph_cfg, batch = synth.coupled_channel(seed=seed, U_o=U_o, c_factor=c_factor, eta_s=eta_s,
+                                           delta_t=k_micro * dt_dpd)
+    M = sph_cfg["substeps"]
+    sp = lhmm.sph_params(sph_cfg["pos"].shape[0], 0, Lx=sph_cfg["Lx"], Ly=sph_cfg["Ly"],
+                         h=sph_cfg["h"], mass=sph_cfg["mass"], rho0=1.0, c=sph_cfg["c"],
+                         theta_pb=0.1, eta_s=eta_s, dt=sph_cfg["dt"],
+                         body_force=(sph_cfg["body_force"], 0.0),
+                         body_mode=lhmm.SPH_BODY_REVERSE_POISEUILLE)
+    sph = lhmm.Sph(sp, sph_cfg["pos"], sph_cfg["vel"])
+    micro = lhmm.Micro.from_batch(lhmm.dpd_params(flow="afbc", seed=seed, alpha=alpha), batch)
+    cpl = lhmm.Coupled(sph, micro, M, k_micro)
+    clo = lhmm.Closure(members=members, in_dim=N_IN, hidden=256, n_hidden=4, out_dim=N_OUT,
+                       seed=closure_seed)
+    return cpl, clo, sph_cfg, M
+
+
+def _rate(cpl, steps):
+    import torch
+    s = torch.cuda.current_stream()
+    cpl.step(2, use_graph=True)  # eager + capture
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    cpl.step(steps, use_graph=True)
+    e1.record(s)
+    e1.synchronize()
+    return steps / (e0.elapsed_time(e1) / 1e3)
+
+
+def surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, batch=4096, n_eval=60,
+                       threshold=0.02, audit_every=50, timing_steps=10, seed=3, alpha=0.01,
+                       U_o=0.25, c_factor=10.0, eta_s=0.1, k_micro=50, dt_dpd=0.01, members=5,
+                       lr=1e-3, weight_decay=1e-4, nbins=16):
+    """Plain LHMM vs surrogate-gated LHMM on the coupled reverse-Poiseuille
+    channel.  Two identical systems run the same `warm + n_data` plain steps
+    (one collects training pairs); the ensemble trains on the GPU; then both run
+    `n_eval` steps (plain vs gated) and the time-averaged y-binned pi_xy and N1
+    profiles are compared.  Returns a dict of rates, errors and counts."""
+    kw = dict(seed=seed, alpha=alpha, U_o=U_o, c_factor=c_factor, eta_s=eta_s, k_micro=k_micro,
+              dt_dpd=dt_dpd, members=members)
+    A, clo_a, cfg, M = _channel(closure_seed=1, **kw)
+    B, clo_b, _, _ = _channel(closure_seed=7, **kw)
+    A.set_closure(clo_a, threshold=threshold, audit_every=audit_every)
+    B.set_closure(clo_b, threshold=threshold, audit_every=audit_every)
+    t0 = time.perf_counter()
+    A.step(warm + n_data, use_graph=True)
+    B.step(warm, use_graph=True)
+    X, T = collect_pairs(B, n_data, skip=0)
+    t_data = time.perf_counter() - t0
+    mean, std, scale = normalization(X, T)
+    clo_b.set_normalization(mean, std, scale)
+    hist, t_train = train(clo_b, X, T, train_steps, batch=batch, lr=lr,
+                          weight_decay=weight_decay, log_every=max(1, train_steps // 10))
+    B.enable_gate(True)
+    Ly = cfg["Ly"]
+    acc = {"A": [np.zeros(nbins), np.zeros(nbins)], "B": [np.zeros(nbins), np.zeros(nbins)]}
+    for _ in range(n_eval):
+        for name, sysm in (("A", A), ("B", B)):
+            sysm.step(1, use_graph=True)
+            y = sysm.sph.get_state()[0][:, 1]
+            _, st = sysm.exchange()
+            pxy, n1 = binned_profiles(y, st, Ly, nbins)
+            acc[name][0] += pxy / n_eval
+            acc[name][1] += n1 / n_eval
+    gs0 = B.gate_stats()
+    rate_plain = _rate(A, timing_steps)
+    rate_gated = _rate(B, timing_steps)
+    gs = B.gate_stats()
+    status = [lhmm.status_string(x.micro.sync(raise_on_error=False)[0]) for x in (A, B)]
+    out = dict(
+        device_status_plain=status[0], device_status_surrogate=status[1],
+        macro_steps_per_s_plain=rate_plain, macro_steps_per_s_surrogate=rate_gated,
+        speedup=rate_gated / rate_plain,
+        stress_error_pxy=rel_l2(acc["B"][0], acc["A"][0]),
+        stress_error_n1=rel_l2(acc["B"][1], acc["A"][1]),
+        dpd_fraction_eval=gs0["dpd_boxes"] / max(1, gs0["gated_steps"] * B.n_boxes),
+        dpd_fraction_timed=(gs["dpd_boxes"] - gs0["dpd_boxes"])
+        / max(1, (gs["gated_steps"] - gs0["gated_steps"]) * B.n_boxes),
+        audit_rel_err=float(np.sqrt(gs["audit_err2"] / max(gs["audit_ref2"], 1e-300))),
+        train_pairs=int(X.shape[0]), train_steps=train_steps, batch=batch,
+        train_loss_first=[float(x) for x in hist[0]] if hist else None,
+        train_loss_last=[float(x) for x in hist[-1]] if hist else None,
+        t_data_s=t_data, t_train_s=t_train, sph_substeps=M, micro_steps=k_micro,
+        boxes=B.n_boxes, threshold=threshold, audit_every=audit_every, n_eval=n_eval,
+        profile_pxy_plain=acc["A"][0].tolist(), profile_pxy_surrogate=acc["B"][0].tolist())
+    for obj in (A, B, clo_a, clo_b):
+        obj.close()
+    return out

@@ -231,21 +231,27 @@ def cylinder_array(n_fluid_target=16384, radius_frac=0.25, wall_layers=None, h_o
     return pos, is_wall, L, dh
 
 
-def coupled_channel(nx=64, ny=32, Ly=4.0, box_beads=1500, seed=3, c_factor=10.0, U_o=1.0,
-                    eta_s=0.5, eta_tot=1.0):
+def coupled_channel(nx=64, ny=32, Ly=4.0, box_beads=1500, seed=3, c_factor=10.0, U_o=0.25,
+                    eta_s=0.1, eta_tot=None, delta_t=0.5):
     """The coupled reverse-Poiseuille workload: an nx x ny SPH channel of height
     Ly (square spacing dh = Ly/ny, Lx = nx dh), Wendland support h = 3 dh, one
     AFBC box of box_beads beads (density 3, 20 % in N_d = 10 chains) per
     particle.  The body force makes the Newtonian mean speed U_o for the total
     viscosity eta_tot (U_o = F rho Ly^2 / (48 eta)); the sound speed is
-    c_factor U_o.  Returns a dict of SPH settings and the box batch (boxes start
-    at rest relative to zero velocity gradient)."""
+    c_factor U_o.  The SPH substeps per exchange interval delta_t follow the
+    CFL rule of Appendix C evaluated with the particle spacing dh as length.
+    Returns a dict of SPH settings and the box batch."""
     pos, Lx, Ly, dh = reverse_poiseuille_channel(nx, ny, Ly)
     n = pos.shape[0]
+    eta_tot = eta_s + 0.01 if eta_tot is None else eta_tot
     F = 48.0 * eta_tot * U_o / Ly ** 2
+    c = c_factor * U_o
+    dt_cfl = 0.25 * min(dh / (1.5 * U_o + c), np.sqrt(dh / F), dh * dh / (2.0 * eta_tot))
+    M = int(np.ceil(delta_t / dt_cfl))
     edge = (box_beads / DENSITY) ** (1.0 / 3.0)
     batch = make_batch(np.full(n, edge), np.zeros((n, 9), np.float32), seed, flow="afbc",
                        n_beads=np.full(n, box_beads))
     sph = dict(pos=pos, vel=np.zeros_like(pos), Lx=Lx, Ly=Ly, dh=dh, h=3.0 * dh,
-               mass=dh * dh, rho0=1.0, c=c_factor * U_o, eta_s=eta_s, body_force=F)
+               mass=dh * dh, rho0=1.0, c=c, eta_s=eta_s, body_force=F, substeps=M,
+               dt=delta_t / M)
     return sph, batch
