@@ -248,6 +248,8 @@ def main():
                     help="boxes of the workload (a smaller case for profilers)")
     ap.add_argument("--micro-steps", type=int, default=100, help="DPD steps per call")
     ap.add_argument("--no-macro", action="store_true", help="skip the coupled macro-step line")
+    ap.add_argument("--no-surrogate", action="store_true",
+                    help="skip the surrogate-gated vs plain comparison")
     ap.add_argument("--uniform-edge", type=float, default=0.0,
                     help="give every box this edge (a one-class case for profilers)")
     args = ap.parse_args()
@@ -359,6 +361,15 @@ def main():
     micro.close()
     if rank == 0 and not args.no_macro and args.uniform_edge <= 0:
         line["secondary"] = macro_step_rate()
+    if rank == 0 and not args.no_surrogate and args.uniform_edge <= 0:
+        from paper_2512_13267_gb300 import closure
+        r = closure.surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, n_eval=60)
+        for k in ("profile_pxy_plain", "profile_pxy_surrogate"):
+            r.pop(k, None)
+        r["metric"] = "LHMM macro-steps/s, surrogate-gated vs plain"
+        r["budget"] = ("bench budget: 150 macro steps of training pairs (307k pairs), 2000 "
+                       "AdamW steps; the configs of DESIGN.md give the full-budget runs")
+        line["surrogate"] = r
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

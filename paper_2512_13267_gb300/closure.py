@@ -46,8 +46,10 @@ def normalization(X, T, floor=1e-6):
     return mean.astype(np.float32), std.astype(np.float32), scale.astype(np.float32)
 
 
-def train(closure, X, T, steps, batch=4096, lr=1e-3, weight_decay=1e-4, seed=0, log_every=0):
-    """AdamW on bootstrap batches (each member draws its own rows).  Returns the
+def train(closure, X, T, steps, batch=4096, lr=1e-3, weight_decay=1e-4, seed=0, log_every=0,
+          cosine=False):
+    """AdamW on bootstrap batches (each member draws its own rows), learning
+    rate lr with cosine decay to zero over `steps` (cosine=True).  Returns the
     per-member loss history (every log_every steps) and the wall time."""
     import torch
     rng = np.random.default_rng(seed)
@@ -65,7 +67,8 @@ def train(closure, X, T, steps, batch=4096, lr=1e-3, weight_decay=1e-4, seed=0, 
         rows = rows_all[k % rows_all.shape[0]]
         if k % rows_all.shape[0] == 0 and k > 0:
             rows_all = torch.randint(0, n, rows_all.shape, dtype=torch.int32, device="cuda")
-        closure.train_step(Xd, Td, batch, lr, weight_decay, rows_dev=rows, loss_dev=loss)
+        lr_k = lr * 0.5 * (1.0 + np.cos(np.pi * k / steps)) if cosine else lr
+        closure.train_step(Xd, Td, batch, lr_k, weight_decay, rows_dev=rows, loss_dev=loss)
         if log_every and (k % log_every == 0 or k == steps - 1):
             hist.append(loss.cpu().numpy().copy())
     torch.cuda.synchronize()
@@ -120,7 +123,7 @@ def _rate(cpl, steps):
 def surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, batch=4096, n_eval=60,
                        threshold=0.02, audit_every=50, timing_steps=10, seed=3, alpha=0.01,
                        U_o=0.25, c_factor=10.0, eta_s=0.1, k_micro=50, dt_dpd=0.01, members=5,
-                       lr=1e-3, weight_decay=1e-4, nbins=16):
+                       lr=1e-3, weight_decay=1e-4, cosine=False, nbins=16):
     """Plain LHMM vs surrogate-gated LHMM on the coupled reverse-Poiseuille
     channel.  Two identical systems run the same `warm + n_data` plain steps
     (one collects training pairs); the ensemble trains on the GPU; then both run
@@ -140,7 +143,8 @@ def surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, batch=4096, n_eval
     mean, std, scale = normalization(X, T)
     clo_b.set_normalization(mean, std, scale)
     hist, t_train = train(clo_b, X, T, train_steps, batch=batch, lr=lr,
-                          weight_decay=weight_decay, log_every=max(1, train_steps // 10))
+                          weight_decay=weight_decay, log_every=max(1, train_steps // 10),
+                          cosine=cosine)
     B.enable_gate(True)
     Ly = cfg["Ly"]
     acc = {"A": [np.zeros(nbins), np.zeros(nbins)], "B": [np.zeros(nbins), np.zeros(nbins)]}
