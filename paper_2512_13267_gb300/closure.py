@@ -180,3 +180,63 @@ def surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, batch=4096, n_eval
     for obj in (A, B, clo_a, clo_b):
         obj.close()
     return out
+
+
+def large_mixed_run(n_fluid=16384, cell=16.0, box_beads=1000, U_o=0.25, c_factor=10.0,
+                    eta_s=0.1, alpha=0.01, k_micro=50, dt_dpd=0.01, seed=5, warm=10, n_data=30,
+                    train_steps=2000, timing_steps=10, threshold=0.02, audit_every=50):
+    """Periodic array of cylinders (radius 0.25 of the cell width) with wall
+    particles, one box of box_beads beads per fluid particle; plain macro
+    steps, then pairs, closure training and surrogate-gated macro steps on the
+    same system (CUDA graphs, autotuned size classes, persistent gated
+    launches).  Returns rates and counts."""
+    import torch
+    from . import synth
+    t_setup = time.perf_counter()
+    pos, is_wall, L, dh = synth.cylinder_array(n_fluid_target=n_fluid, radius_frac=0.25, cell=cell)
+    n = pos.shape[0]
+    n_wall = int(is_wall.sum())
+    eta_tot = eta_s + 0.01
+    F = 48.0 * eta_tot * U_o / L ** 2
+    c = c_factor * U_o
+    delta_t = k_micro * dt_dpd
+    dt_cfl = 0.25 * min(dh / (1.5 * U_o + c), np.sqrt(dh / F), dh * dh / (2.0 * eta_tot))
+    M = int(np.ceil(delta_t / dt_cfl))
+    sp = lhmm.sph_params(n, n_wall, Lx=L, Ly=L, h=3 * dh, mass=dh * dh, rho0=1.0, c=c,
+                         theta_pb=0.1, eta_s=eta_s, dt=delta_t / M, body_force=(F, 0.0),
+                         body_mode=lhmm.SPH_BODY_UNIFORM)
+    sph = lhmm.Sph(sp, pos, np.zeros_like(pos))
+    edge = (box_beads / synth.DENSITY) ** (1.0 / 3.0)
+    batch = synth.make_batch(np.full(n_fluid, edge), np.zeros((n_fluid, 9), np.float32), seed,
+                             flow="afbc", n_beads=np.full(n_fluid, box_beads))
+    micro = lhmm.Micro.from_batch(lhmm.dpd_params(flow="afbc", seed=seed, alpha=alpha), batch)
+    L0 = torch.zeros((n_fluid, 9), dtype=torch.float32, device="cuda")
+    micro.autotune(L0, probe_steps=5)
+    cpl = lhmm.Coupled(sph, micro, M, k_micro)
+    clo = lhmm.Closure(members=5, in_dim=N_IN, hidden=256, n_hidden=4, out_dim=N_OUT, seed=seed)
+    cpl.set_closure(clo, threshold=threshold, audit_every=audit_every)
+    t_setup = time.perf_counter() - t_setup
+    cpl.step(warm, use_graph=True)
+    rate_plain = _rate(cpl, timing_steps)
+    X, T = collect_pairs(cpl, n_data, skip=HIST)
+    mean, std, scale = normalization(X, T)
+    clo.set_normalization(mean, std, scale)
+    _, t_train = train(clo, X, T, train_steps)
+    cpl.enable_gate(True)
+    g0 = cpl.gate_stats()
+    rate_gated = _rate(cpl, timing_steps)
+    g1 = cpl.gate_stats()
+    status = lhmm.status_string(micro.sync(raise_on_error=False)[0])
+    out = dict(workload="periodic cylinder array: cell %.0f, radius 0.25 cell, %d fluid + %d wall SPH "
+                        "particles, %d-bead AFBC boxes (%d beads), k'=%d, M=%d"
+                        % (L, n_fluid, n_wall, box_beads, batch.total_beads, k_micro, M),
+               macro_steps_per_s_plain=rate_plain, macro_steps_per_s_surrogate=rate_gated,
+               speedup=rate_gated / rate_plain,
+               bead_steps_per_s_plain=rate_plain * batch.total_beads * k_micro,
+               dpd_fraction=(g1["dpd_boxes"] - g0["dpd_boxes"])
+               / max(1, (g1["gated_steps"] - g0["gated_steps"]) * n_fluid),
+               train_pairs=int(X.shape[0]), train_steps=train_steps, t_train_s=t_train,
+               t_setup_s=t_setup, device_status=status, launch_plan=micro.plan())
+    for o in (cpl, clo, micro, sph):
+        o.close()
+    return out

@@ -205,15 +205,17 @@ def reverse_poiseuille_channel(nx=64, ny=32, Ly=4.0):
     return pos, Lx, Ly, dh
 
 
-def cylinder_array(n_fluid_target=16384, radius_frac=0.25, wall_layers=None, h_over_dh=3.0):
-    """Periodic cell with one cylinder of radius radius_frac * cell width
-    (Sec. 6.2 geometry).  Returns (pos, is_wall, L, dh): lattice particles
-    outside the cylinder are fluid; those inside within h of its surface are
-    fixed wall particles; the rest of the cylinder is empty."""
+def cylinder_array(n_fluid_target=16384, radius_frac=0.25, wall_layers=None, h_over_dh=3.0,
+                   cell=1.0):
+    """Periodic cell of width `cell` with one cylinder of radius radius_frac *
+    cell (Sec. 6.2 geometry).  Returns (pos, is_wall, L, dh): lattice particles
+    outside the cylinder are fluid (exactly n_fluid_target, first); those
+    inside within h of its surface are fixed wall particles (last); the rest of
+    the cylinder is empty."""
     area_frac = 1.0 - np.pi * radius_frac ** 2
     n_side = int(np.ceil(np.sqrt(n_fluid_target / area_frac)))
     while True:
-        L = 1.0
+        L = float(cell)
         dh = L / n_side
         pos = sph_lattice(n_side, n_side, L, L)
         r = np.hypot(pos[:, 0] - 0.5 * L, pos[:, 1] - 0.5 * L)
