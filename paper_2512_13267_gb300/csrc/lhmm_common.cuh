@@ -39,11 +39,23 @@ __device__ __forceinline__ uint2 philox4x32_10_xy(uint32_t c0, uint32_t c1, uint
 }
 
 // Standard normal from two words: u = (k + 1/2) 2^-23 with k the top 23 bits
-// (exact in FP32), then Box-Muller with the accurate library functions.
+// (exact in FP32, u in (0, 1)), then Box-Muller r cos(2 pi u2) with
+// r = sqrt(-2 ln u1).  ln u1 uses the hardware log2 for u1 <= 3/4 and above it
+// the series ln u = 2 artanh(z) = 2 (z + z^3/3 + z^5/5 + z^7/7 + z^9/9) with
+// z = (u - 1)/(u + 1) in (-1/7, 0] (truncation below 4e-10 relative), so
+// -2 ln u1 keeps its relative precision as u1 -> 1 where the hardware log2
+// only has an absolute bound.  The hardware cosine is accurate on [-pi, pi],
+// hence cos(2 pi u2) = -cos(2 pi (u2 - 1/2)).
 __device__ __forceinline__ float gauss_from_words(uint32_t x0, uint32_t x1) {
   const float u1 = (static_cast<float>(x0 >> 9) + 0.5f) * 0x1p-23f;
   const float u2 = (static_cast<float>(x1 >> 9) + 0.5f) * 0x1p-23f;
-  return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+  const float z = __fdividef(u1 - 1.f, u1 + 1.f);
+  const float z2 = z * z;
+  const float poly =
+      fmaf(z2, fmaf(z2, fmaf(z2, fmaf(z2, 1.f / 9.f, 1.f / 7.f), 1.f / 5.f), 1.f / 3.f), 1.f);
+  const float ln_u1 = u1 > 0.75f ? 2.f * z * poly : __log2f(u1) * 0.693147181f;
+  const float s = -2.f * ln_u1;  // >= 1.19e-7: u1 <= 1 - 2^-24
+  return -(s * rsqrtf(s)) * __cosf(6.283185307f * (u2 - 0.5f));
 }
 
 template <typename T>

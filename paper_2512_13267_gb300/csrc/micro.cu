@@ -8,12 +8,14 @@
 // kernel is bound by on-chip arithmetic.  Every step the block
 //   A  half-kicks and drifts its beads, re-normalising cell-relative offsets
 //      and applying Lees-Edwards re-entry (Sec. 2.3 VV; coupling Step 3);
-//   B  rebuilds a counting-sort cell list (cells >= rc wide) with a
-//      deterministic order inside each cell;
+//   B  rebuilds a counting-sort cell list (cells >= rc wide) ordered by
+//      (x, id) inside each cell, so every row of cells is sorted by x;
 //   C  sums DPD conservative, dissipative and random pair forces (Eqs.
-//      conservative, dissipative, random) over the 27 neighbour cells plus the
-//      FENE bonds (Eq. fene_force), accumulating the pair virial of the IK
-//      potential stress (Eq. potential_stress) with the core bond fraction;
+//      conservative, dissipative, random) over the upper half of the 27
+//      neighbour cells, each neighbour row cut to the x window that the
+//      bead's y, z distance to the row leaves inside rc, plus the FENE bonds
+//      (Eq. fene_force), accumulating the pair virial of the IK potential
+//      stress (Eq. potential_stress) with the core bond fraction;
 //   D  half-kicks, imposes v = lambda* L r' on the AFBC BC shell (Eq.
 //      micro_bc), accumulates the IK kinetic stress (Eq. kinetic_stress) and
 //      block-reduces the step's stress; the time average (N'_t = k') is kept
@@ -100,6 +102,7 @@ __host__ __device__ inline size_t micro_smem_bytes(int N, int C, int T) {
   b = align16(b);
   b += sizeof(unsigned long long) * (size_t)kQueue * (T / 32);  // pair queues
   b += sizeof(float) * kRedFloats;
+  b += sizeof(double) * 12;  // FP64 stress sums
   return b;
 }
 
@@ -117,30 +120,24 @@ __device__ __forceinline__ float seg_fraction(float ax, float ay, float az, floa
   const float a[3] = {ax, ay, az}, d[3] = {bx - ax, by - ay, bz - az};
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    if (d[k] == 0.f) {
-      if (!(fabsf(a[k]) < h[k])) return 0.f;
-      continue;
-    }
-    const float inv = 1.f / d[k];
+    // parameter interval of the slab |a + s d| < h (approximate reciprocal:
+    // the weight needs a few ulp, not a correctly rounded quotient)
+    const bool flat = d[k] == 0.f;
+    const float inv = __fdividef(1.f, flat ? 1.f : d[k]);
     const float s1 = (-h[k] - a[k]) * inv, s2 = (h[k] - a[k]) * inv;
-    lo = fmaxf(lo, fminf(s1, s2));
-    hi = fminf(hi, fmaxf(s1, s2));
+    const bool in = fabsf(a[k]) < h[k];
+    lo = fmaxf(lo, flat ? (in ? 0.f : 2.f) : fminf(s1, s2));
+    hi = fminf(hi, flat ? (in ? 1.f : -1.f) : fmaxf(s1, s2));
   }
   return hi > lo ? hi - lo : 0.f;
 }
 
-// A queued pair: bead i, bead j, the image of j relative to i as neighbour
-// cell offsets (x may exceed one cell in a Lees-Edwards shifted row), the IK
-// bond-weight mode of i and the Lees-Edwards crossing of the row.
-__device__ __forceinline__ unsigned long long pack_pair(int i, int j, int dcx, int dy, int dz,
-                                                        int ikm, int cross) {
-  return static_cast<unsigned long long>(i) | (static_cast<unsigned long long>(j) << 16) |
-         (static_cast<unsigned long long>(dcx & 0xff) << 32) |
-         (static_cast<unsigned long long>(dy + 1) << 40) |
-         (static_cast<unsigned long long>(dz + 1) << 42) |
-         (static_cast<unsigned long long>(ikm) << 44) |
-         (static_cast<unsigned long long>(cross) << 46);
-}
+// A queued pair is one 64-bit word: bead i (bits 0-15), bead j (16-31), the
+// x cell offset of j's image relative to i plus 128 (32-39; the offset may
+// exceed one cell in a Lees-Edwards shifted row, |offset| < 2 nx + 3 < 128),
+// dy + 1 (40-41), dz + 1 (42-43), the IK bond-weight mode of i (44-45) and
+// the Lees-Edwards crossing of the row (46-47).
+constexpr int kDcxBias = 128;
 
 struct BoxView {
   float *ox, *oy, *oz, *vx, *vy, *vz, *fx, *fy, *fz;
@@ -225,7 +222,10 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
   const float hx = 0.5f * sB.len[0], hy = 0.5f * sB.len[1], hz = 0.5f * sB.len[2];
   const unsigned lt_mask = (1u << lane) - 1u;
   unsigned status = 0;
-  double acc_sum = 0.0, acc_sq = 0.0;  // threads 0..5 own one stress component each
+  // FP64 stress sums (component k by thread k) live in shared memory: they
+  // would otherwise hold four registers of every thread across the step loop
+  double* acc = reinterpret_cast<double*>(red + kRedFloats);
+  if (tid < 12) acc[tid] = 0.0;
 
   const int total_steps = A.init_forces ? 1 : A.n_steps;
   for (int s = 0; s < total_steps; ++s) {
@@ -344,13 +344,17 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
       perm[cstart[c] + rank] = static_cast<unsigned short>(i);
     }
     __syncthreads();
-    for (int c = tid; c < C; c += T) {  // ascending ids inside each cell
+    for (int c = tid; c < C; c += T) {  // ascending (x, id) inside each cell
       const int s0 = cstart[c], s1 = cstart[c + 1];
       for (int p = s0 + 1; p < s1; ++p) {
         const unsigned short key = perm[p];
+        const float kx = ox[key];
         int q = p - 1;
-        while (q >= s0 && perm[q] > key) {
-          perm[q + 1] = perm[q];
+        while (q >= s0) {
+          const unsigned short o = perm[q];
+          const float x = ox[o];
+          if (!(x > kx || (x == kx && o > key))) break;
+          perm[q + 1] = o;
           --q;
         }
         perm[q + 1] = key;
@@ -368,7 +372,7 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
     float W[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     auto eval_pair = [&](unsigned long long e) {
       const int i = static_cast<int>(e & 0xffffu), j = static_cast<int>((e >> 16) & 0xffffu);
-      const int dcx = static_cast<int>(static_cast<signed char>((e >> 32) & 0xffu));
+      const int dcx = static_cast<int>((e >> 32) & 0xffu) - kDcxBias;
       const int dy = static_cast<int>((e >> 40) & 3u) - 1, dz = static_cast<int>((e >> 42) & 3u) - 1;
       const int ikm = static_cast<int>((e >> 44) & 3u), cross = static_cast<int>((e >> 46) & 3u);
       const float sx = cross == 1 ? le_off : (cross == 2 ? -le_off : 0.f);
@@ -444,20 +448,25 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
           ikm = (m >= A.rc) ? 0 : ((m < -A.rc) ? 1 : 2);
         }
       }
-      // upper-half rows: (dz, dy) = (0,0) [own cell after slot k, next x cell],
-      // (0,+1), (+1,-1), (+1,0), (+1,+1) [three x cells each]
+      // upper-half rows of cells: (dz, dy) = (0,0) [slots after k up to
+      // x_i + rc], (0,+1), (+1,-1), (+1,0), (+1,+1) [an x window each]
       for (int row = 0; row < 5; ++row) {
         const int dz = row < 2 ? 0 : 1;
         const int dy = row == 0 ? 0 : (row == 1 ? 1 : row - 3);
-        // up to two slot ranges; inside a range, cell boundaries e0, e1 give
-        // the candidate's x cell as ua + (q >= e0) + (q >= e1)
-        int s1 = 0, len1 = 0, e01 = 0, e11 = 0, ua1 = 0;
-        int s2 = 0, len2 = 0, e02 = 0, e12 = 0, ua2 = 0;
-        int cross = 0;
-        float sxr = 0.f;
+        // up to two slot ranges (two when the row wraps in x); per range the
+        // first slot, the length, the slots e0, e1 where its 2nd and 3rd x
+        // cells start, the x cell offset dc of its first cell (j's image
+        // relative to i) and xb = x_i - dc*wx - shift, so that for slot q
+        // rx = xb - wx*[(q >= e0) + (q >= e1)] - ox[j]
+        int s1 = 0, len1 = 0, e01 = 0, e11 = 0;
+        int s2 = 0, len2 = 0, e02 = 0, e12 = 0;
+        float xb1 = 0.f, xb2 = 0.f;
+        unsigned hw1 = 0u, hw2 = 0u;  // upper word of the range's queue entries at dc
         if (own) {
           const int z = wrapi(cz + dz, nz);
           int y = cy + dy;
+          int cross = 0;
+          float sxr = 0.f;
           if (y < 0) {
             y += ny;
             if (le) { cross = 2; sxr = -le_off; }
@@ -465,62 +474,116 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
             y -= ny;
             if (le) { cross = 1; sxr = le_off; }
           }
-          const int rowbase = nx * (y + ny * z);
-          int ulo, uhi;
-          if (row == 0) {
-            ulo = cx;
-            uhi = cx + 1;
-          } else if (cross) {  // images slide by sxr: cells covering x_i - sxr +- rc
-            const float xt = static_cast<float>(cx) * wx + xi - sxr;
-            ulo = static_cast<int>(floorf((xt - A.rc) * sB.winv[0]));
-            uhi = min(static_cast<int>(floorf((xt + A.rc) * sB.winv[0])), ulo + 2);
-          } else {
-            ulo = cx - 1;
-            uhi = cx + 1;
-          }
-          const int wlo = ((ulo % nx) + nx) % nx, whi = ((uhi % nx) + nx) % nx;
-          const bool single = (wlo <= whi) && (whi - wlo == uhi - ulo);
-          const int wend1 = single ? whi : nx - 1;
-          ua1 = ulo;
-          s1 = (row == 0) ? k + 1 : cstart[rowbase + wlo];
-          e01 = cstart[rowbase + min(wlo + 1, wend1 + 1)];
-          e11 = cstart[rowbase + min(wlo + 2, wend1 + 1)];
-          if (wlo + 1 > wend1) e01 = 0x7fffffff;
-          if (wlo + 2 > wend1) e11 = 0x7fffffff;
-          len1 = cstart[rowbase + wend1 + 1] - s1;
-          if (!single) {
-            ua2 = uhi - whi;
-            s2 = cstart[rowbase];
-            e02 = whi >= 1 ? cstart[rowbase + 1] : 0x7fffffff;
-            e12 = whi >= 2 ? cstart[rowbase + 2] : 0x7fffffff;
-            len2 = cstart[rowbase + whi + 1] - s2;
+          // Beads of the row's cell column within rc of i lie within
+          // |x_j - c| < w of the (image-shifted) centre c = x_i - sxr, where
+          // w^2 = rc^2 - ey^2 - ez^2 and ey, ez are i's distances to the
+          // column in y and z; the row is sorted by x, so the candidates
+          // are one slot window (two where it wraps around the row).
+          const float ey = dy > 0 ? wy - yi : (dy < 0 ? yi : 0.f);
+          const float ez = dz > 0 ? wz - zi : 0.f;
+          const float w2 = A.rc2 - ey * ey - ez * ez;
+          if (w2 > 0.f) {
+            const unsigned hiw = (static_cast<unsigned>(dy + 1) << 8) |
+                                 (static_cast<unsigned>(dz + 1) << 10) |
+                                 (static_cast<unsigned>(ikm) << 12) |
+                                 (static_cast<unsigned>(cross) << 14);
+            const int rowbase = nx * (y + ny * z);
+            const float lenx = sB.len[0];
+            // first slot of the row with x >= X (X in [0, lenx]); also the
+            // cell that holds X
+            auto lower = [&](float X, int& cell) -> int {
+              const int c = min(__float2int_rd(X * sB.winv[0]), nx - 1);
+              const float xr = X - static_cast<float>(c) * wx;
+              int q = cstart[rowbase + c];
+              const int qe = cstart[rowbase + c + 1];
+              while (q < qe && ox[perm[q]] < xr) ++q;
+              cell = c;
+              return q;
+            };
+            // a range from slot q0 (inside x cell ca, image m of the row)
+            // to slot q1: the x offset of its first cell relative to i, the
+            // cell boundaries after it, and the x base of rx
+            auto set_range = [&](int q0, int q1, int ca, int m, int& sr, int& lr, int& e0r,
+                                 int& e1r, float& xbr, unsigned& hwr) {
+              const int dc = ca + m * nx - cx;
+              sr = q0;
+              lr = max(q1 - q0, 0);
+              e0r = ca + 1 <= nx ? cstart[rowbase + ca + 1] : 0x7fffffff;
+              e1r = ca + 2 <= nx ? cstart[rowbase + ca + 2] : 0x7fffffff;
+              xbr = (-static_cast<float>(dc) * wx - sxr) + xi;
+              hwr = hiw + static_cast<unsigned>(dc + kDcxBias);
+            };
+            const float xa = static_cast<float>(cx) * wx + xi;
+            const int rowstart = cstart[rowbase], rowend = cstart[rowbase + nx];
+            if (row == 0) {  // after slot k up to x_i + rc, around the row
+              const float X1 = xa + A.rc + 1e-5f;
+              int c1;
+              if (X1 <= lenx) {
+                const int q1 = lower(X1, c1);
+                set_range(k + 1, q1, cx, 0, s1, len1, e01, e11, xb1, hw1);
+              } else {
+                const int q1 = lower(X1 - lenx, c1);
+                set_range(k + 1, rowend, cx, 0, s1, len1, e01, e11, xb1, hw1);
+                set_range(rowstart, q1, 0, 1, s2, len2, e02, e12, xb2, hw2);
+              }
+            } else {
+              const float w = sqrtf(w2) + 1e-5f;
+              float cc = xa - sxr;  // in (-lenx, 2 lenx)
+              int m0 = 0;
+              if (cc < 0.f) { cc += lenx; m0 = -1; }
+              else if (cc >= lenx) { cc -= lenx; m0 = 1; }
+              const float X0 = cc - w, X1 = cc + w;
+              int c0, c1;
+              if (X0 < 0.f) {  // wraps below: [X0 + len, len) of image m0 - 1, [0, X1) of m0
+                const int q0 = lower(X0 + lenx, c0);
+                const int q1 = lower(X1, c1);
+                set_range(q0, rowend, c0, m0 - 1, s1, len1, e01, e11, xb1, hw1);
+                set_range(rowstart, q1, 0, m0, s2, len2, e02, e12, xb2, hw2);
+              } else if (X1 > lenx) {  // wraps above: [X0, len) of m0, [0, X1 - len) of m0 + 1
+                const int q0 = lower(X0, c0);
+                const int q1 = lower(X1 - lenx, c1);
+                set_range(q0, rowend, c0, m0, s1, len1, e01, e11, xb1, hw1);
+                set_range(rowstart, q1, 0, m0 + 1, s2, len2, e02, e12, xb2, hw2);
+              } else {
+                const int q0 = lower(X0, c0);
+                const int q1 = lower(X1, c1);
+                set_range(q0, q1, c0, m0, s1, len1, e01, e11, xb1, hw1);
+              }
+            }
           }
         }
         const int len = len1 + len2;
         const int lmax = __reduce_max_sync(FULL, len);
-        const float byr = -static_cast<float>(dy) * wy, bzr = -static_cast<float>(dz) * wz;
+        const float yb = -static_cast<float>(dy) * wy + yi, zb = -static_cast<float>(dz) * wz + zi;
+        const unsigned lo_i = static_cast<unsigned>(i);
+        const int s2o = s2 - len1;
         for (int t = 0; t < lmax; ++t) {
           bool hit = false;
-          int q = 0, dcx = 0;
+          unsigned lo_w = 0u, hi_w = 0u;
           if (t < len) {
             const bool first = t < len1;
-            q = first ? s1 + t : s2 + (t - len1);
-            const int e0 = first ? e01 : e02, e1 = first ? e11 : e12;
-            dcx = (first ? ua1 : ua2) + (q >= e0) + (q >= e1) - cx;
+            const int q = t + (first ? s1 : s2o);
+            const bool p0 = q >= (first ? e01 : e02), p1 = q >= (first ? e11 : e12);
+            float bx = first ? xb1 : xb2;
+            bx = p0 ? bx - wx : bx;
+            bx = p1 ? bx - wx : bx;
             const int j = perm[q];
-            const float rx = (-static_cast<float>(dcx) * wx - sxr) + (xi - ox[j]);
-            const float ry = byr + (yi - oy[j]);
-            const float rz = bzr + (zi - oz[j]);
+            const float rx = bx - ox[j];
+            const float ry = yb - oy[j];
+            const float rz = zb - oz[j];
             const float r2 = rx * rx + ry * ry + rz * rz;
             hit = (r2 < A.rc2) && (r2 > 0.f);
             if (hit && !A.dpd_on_bonded) {
               const int lo = min(i, j), hi = max(i, j);
               if (hi == lo + 1 && hi < sB.n_poly && (hi % A.chain_len) != 0) hit = false;
             }
-            q = j;
+            lo_w = lo_i | (static_cast<unsigned>(j) << 16);
+            hi_w = (first ? hw1 : hw2) + static_cast<unsigned>(p0) + static_cast<unsigned>(p1);
           }
           const unsigned bal = __ballot_sync(FULL, hit);
-          if (hit) queue[count + __popc(bal & lt_mask)] = pack_pair(i, q, dcx, dy, dz, ikm, cross);
+          if (hit)
+            queue[count + __popc(bal & lt_mask)] =
+                (static_cast<unsigned long long>(hi_w) << 32) | lo_w;
           count += __popc(bal);
           if (count >= 32) {
             __syncwarp();
@@ -648,8 +711,8 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
       float sum = 0.f;
       for (int w = 0; w < NW; ++w) sum += red[6 * w + tid];
       const double pi = -static_cast<double>(sum) * static_cast<double>(sB.inv_vcore);
-      acc_sum += pi;
-      acc_sq += pi * pi;
+      acc[tid] += pi;
+      acc[6 + tid] += pi * pi;
     }
     __syncthreads();
   }
@@ -669,8 +732,8 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
   if (!A.init_forces && A.n_steps > 0) {
     if (tid < 6) {
       const double inv = 1.0 / static_cast<double>(A.n_steps);
-      A.stress[6 * bid + tid] = A.out_scale * acc_sum * inv;
-      if (A.stress_sq) A.stress_sq[6 * bid + tid] = A.out_scale * A.out_scale * acc_sq * inv;
+      A.stress[6 * bid + tid] = A.out_scale * acc[tid] * inv;
+      if (A.stress_sq) A.stress_sq[6 * bid + tid] = A.out_scale * A.out_scale * acc[6 + tid] * inv;
     }
     if (tid == 0) {
       A.state[bid].step = step0 + static_cast<unsigned long long>(A.n_steps);
