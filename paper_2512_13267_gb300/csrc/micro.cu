@@ -428,129 +428,130 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
       }
     };
 
+    // Work items are (chunk of 32 consecutive sorted slots, row) pairs; each
+    // warp takes a contiguous share of them, so the block stays balanced when
+    // the bead count is not a multiple of the block size.
     int count = 0;  // warp-uniform queue fill
-    const int rounds = (N + T - 1) / T;
-    for (int rd = 0; rd < rounds; ++rd) {
-      const int k = tid + rd * T;
-      const bool own = k < N;
-      const int i = own ? perm[k] : 0;
-      int cx = 0, cy = 0, cz = 0, ikm = 1;
-      float xi = 0.f, yi = 0.f, zi = 0.f;
-      if (own) {
-        cell_coords(cellid[i], nx, nxy, inx, inxy, cx, cy, cz);
-        xi = ox[i]; yi = oy[i]; zi = oz[i];
-        const float rpx = static_cast<float>(cx) * wx + xi - hx;
-        const float rpy = static_cast<float>(cy) * wy + yi - hy;
-        const float rpz = static_cast<float>(cz) * wz + zi - hz;
-        if (afbc) {  // a pair segment reaches at most rc from bead i (max norm)
-          const float m = fmaxf(fabsf(rpx) - sB.half_core[0],
-                                fmaxf(fabsf(rpy) - sB.half_core[1], fabsf(rpz) - sB.half_core[2]));
-          ikm = (m >= A.rc) ? 0 : ((m < -A.rc) ? 1 : 2);
+    const int n_items = 5 * ((N + 31) >> 5);
+    const int per_warp = (n_items + NW - 1) / NW;
+    const int it_end = min(n_items, (warp + 1) * per_warp);
+    int cur_chunk = -1;
+    int k = 0, i = 0, cx = 0, cy = 0, cz = 0, ikm = 1;
+    float xi = 0.f, yi = 0.f, zi = 0.f;
+    for (int it = warp * per_warp; it < it_end; ++it) {
+      const int chunk = it / 5, row = it - 5 * chunk;
+      if (chunk != cur_chunk) {  // warp-uniform: load bead k = 32 chunk + lane
+        cur_chunk = chunk;
+        k = (chunk << 5) + lane;
+        const bool own = k < N;
+        i = own ? perm[k] : 0;
+        cx = cy = cz = 0;
+        ikm = 1;
+        xi = yi = zi = 0.f;
+        if (own) {
+          cell_coords(cellid[i], nx, nxy, inx, inxy, cx, cy, cz);
+          xi = ox[i]; yi = oy[i]; zi = oz[i];
+          if (afbc) {  // a pair segment reaches at most rc from bead i (max norm)
+            const float rpx = static_cast<float>(cx) * wx + xi - hx;
+            const float rpy = static_cast<float>(cy) * wy + yi - hy;
+            const float rpz = static_cast<float>(cz) * wz + zi - hz;
+            const float m = fmaxf(fabsf(rpx) - sB.half_core[0],
+                                  fmaxf(fabsf(rpy) - sB.half_core[1], fabsf(rpz) - sB.half_core[2]));
+            ikm = (m >= A.rc) ? 0 : ((m < -A.rc) ? 1 : 2);
+          }
         }
       }
-      // upper-half rows of cells: (dz, dy) = (0,0) [slots after k up to
-      // x_i + rc], (0,+1), (+1,-1), (+1,0), (+1,+1) [an x window each]
-      for (int row = 0; row < 5; ++row) {
+      {
+        // upper-half rows of cells: (dz, dy) = (0,0) [slots after k up to
+        // x_i + rc], (0,+1), (+1,-1), (+1,0), (+1,+1) [an x window each]
         const int dz = row < 2 ? 0 : 1;
         const int dy = row == 0 ? 0 : (row == 1 ? 1 : row - 3);
-        // up to two slot ranges (two when the row wraps in x); per range the
-        // first slot, the length, the slots e0, e1 where its 2nd and 3rd x
-        // cells start, the x cell offset dc of its first cell (j's image
-        // relative to i) and xb = x_i - dc*wx - shift, so that for slot q
-        // rx = xb - wx*[(q >= e0) + (q >= e1)] - ox[j]
+        // up to two slot ranges (two when the window wraps around the row);
+        // per range the first slot, the length, the slots e0, e1 where its
+        // 2nd and 3rd x cells start, and xb = x_i - dc*wx - shift with dc the
+        // x cell offset of its first cell (j's image relative to i), so that
+        // for slot q rx = xb - wx*[(q >= e0) + (q >= e1)] - ox[j]
         int s1 = 0, len1 = 0, e01 = 0, e11 = 0;
         int s2 = 0, len2 = 0, e02 = 0, e12 = 0;
         float xb1 = 0.f, xb2 = 0.f;
         unsigned hw1 = 0u, hw2 = 0u;  // upper word of the range's queue entries at dc
-        if (own) {
-          const int z = wrapi(cz + dz, nz);
-          int y = cy + dy;
-          int cross = 0;
-          float sxr = 0.f;
-          if (y < 0) {
-            y += ny;
-            if (le) { cross = 2; sxr = -le_off; }
-          } else if (y >= ny) {
-            y -= ny;
-            if (le) { cross = 1; sxr = le_off; }
-          }
-          // Beads of the row's cell column within rc of i lie within
-          // |x_j - c| < w of the (image-shifted) centre c = x_i - sxr, where
-          // w^2 = rc^2 - ey^2 - ez^2 and ey, ez are i's distances to the
-          // column in y and z; the row is sorted by x, so the candidates
-          // are one slot window (two where it wraps around the row).
-          const float ey = dy > 0 ? wy - yi : (dy < 0 ? yi : 0.f);
-          const float ez = dz > 0 ? wz - zi : 0.f;
-          const float w2 = A.rc2 - ey * ey - ez * ez;
-          if (w2 > 0.f) {
-            const unsigned hiw = (static_cast<unsigned>(dy + 1) << 8) |
-                                 (static_cast<unsigned>(dz + 1) << 10) |
-                                 (static_cast<unsigned>(ikm) << 12) |
-                                 (static_cast<unsigned>(cross) << 14);
-            const int rowbase = nx * (y + ny * z);
-            const float lenx = sB.len[0];
-            // first slot of the row with x >= X (X in [0, lenx]); also the
-            // cell that holds X
-            auto lower = [&](float X, int& cell) -> int {
-              const int c = min(__float2int_rd(X * sB.winv[0]), nx - 1);
-              const float xr = X - static_cast<float>(c) * wx;
-              int q = cstart[rowbase + c];
-              const int qe = cstart[rowbase + c + 1];
-              while (q < qe && ox[perm[q]] < xr) ++q;
-              cell = c;
-              return q;
-            };
-            // a range from slot q0 (inside x cell ca, image m of the row)
-            // to slot q1: the x offset of its first cell relative to i, the
-            // cell boundaries after it, and the x base of rx
-            auto set_range = [&](int q0, int q1, int ca, int m, int& sr, int& lr, int& e0r,
-                                 int& e1r, float& xbr, unsigned& hwr) {
-              const int dc = ca + m * nx - cx;
-              sr = q0;
-              lr = max(q1 - q0, 0);
-              e0r = ca + 1 <= nx ? cstart[rowbase + ca + 1] : 0x7fffffff;
-              e1r = ca + 2 <= nx ? cstart[rowbase + ca + 2] : 0x7fffffff;
-              xbr = (-static_cast<float>(dc) * wx - sxr) + xi;
-              hwr = hiw + static_cast<unsigned>(dc + kDcxBias);
-            };
-            const float xa = static_cast<float>(cx) * wx + xi;
-            const int rowstart = cstart[rowbase], rowend = cstart[rowbase + nx];
-            if (row == 0) {  // after slot k up to x_i + rc, around the row
-              const float X1 = xa + A.rc + 1e-5f;
-              int c1;
-              if (X1 <= lenx) {
-                const int q1 = lower(X1, c1);
-                set_range(k + 1, q1, cx, 0, s1, len1, e01, e11, xb1, hw1);
+        const int z = wrapi(cz + dz, nz);
+        int y = cy + dy;
+        int cross = 0;
+        float sxr = 0.f;
+        if (y < 0) {
+          y += ny;
+          if (le) { cross = 2; sxr = -le_off; }
+        } else if (y >= ny) {
+          y -= ny;
+          if (le) { cross = 1; sxr = le_off; }
+        }
+        // Beads of the row's cell column within rc of i lie within |x_j - c|
+        // < w of the (image-shifted) centre c = x_i - sxr, where w^2 = rc^2 -
+        // ey^2 - ez^2 and ey, ez are i's distances to the column in y and z;
+        // the row is sorted by x, so the candidates are one slot window (two
+        // where it wraps around the row).
+        const float ey = dy > 0 ? wy - yi : (dy < 0 ? yi : 0.f);
+        const float ez = dz > 0 ? wz - zi : 0.f;
+        const float w2 = A.rc2 - ey * ey - ez * ez;
+        if (k < N && w2 > 0.f) {
+          const float lenx = sB.len[0], winvx = sB.winv[0];
+          const float xa = static_cast<float>(cx) * wx + xi;
+          const unsigned hiw = (static_cast<unsigned>(dy + 1) << 8) |
+                               (static_cast<unsigned>(dz + 1) << 10) |
+                               (static_cast<unsigned>(ikm) << 12) |
+                               (static_cast<unsigned>(cross) << 14);
+          const int rowbase = nx * (y + ny * z);
+          // first slot of the row with x >= X (X in [0, lenx]; binary search
+          // inside the cell that holds X), and that cell
+          auto lower = [&](float X, int& cell) -> int {
+            const int c = min(__float2int_rd(X * winvx), nx - 1);
+            const float xr = X - static_cast<float>(c) * wx;
+            int lo = cstart[rowbase + c];
+            int n = cstart[rowbase + c + 1] - lo;
+            while (n > 0) {
+              const int half = n >> 1;
+              if (ox[perm[lo + half]] < xr) {
+                lo += half + 1;
+                n -= half + 1;
               } else {
-                const int q1 = lower(X1 - lenx, c1);
-                set_range(k + 1, rowend, cx, 0, s1, len1, e01, e11, xb1, hw1);
-                set_range(rowstart, q1, 0, 1, s2, len2, e02, e12, xb2, hw2);
-              }
-            } else {
-              const float w = sqrtf(w2) + 1e-5f;
-              float cc = xa - sxr;  // in (-lenx, 2 lenx)
-              int m0 = 0;
-              if (cc < 0.f) { cc += lenx; m0 = -1; }
-              else if (cc >= lenx) { cc -= lenx; m0 = 1; }
-              const float X0 = cc - w, X1 = cc + w;
-              int c0, c1;
-              if (X0 < 0.f) {  // wraps below: [X0 + len, len) of image m0 - 1, [0, X1) of m0
-                const int q0 = lower(X0 + lenx, c0);
-                const int q1 = lower(X1, c1);
-                set_range(q0, rowend, c0, m0 - 1, s1, len1, e01, e11, xb1, hw1);
-                set_range(rowstart, q1, 0, m0, s2, len2, e02, e12, xb2, hw2);
-              } else if (X1 > lenx) {  // wraps above: [X0, len) of m0, [0, X1 - len) of m0 + 1
-                const int q0 = lower(X0, c0);
-                const int q1 = lower(X1 - lenx, c1);
-                set_range(q0, rowend, c0, m0, s1, len1, e01, e11, xb1, hw1);
-                set_range(rowstart, q1, 0, m0 + 1, s2, len2, e02, e12, xb2, hw2);
-              } else {
-                const int q0 = lower(X0, c0);
-                const int q1 = lower(X1, c1);
-                set_range(q0, q1, c0, m0, s1, len1, e01, e11, xb1, hw1);
+                n = half;
               }
             }
+            cell = c;
+            return lo;
+          };
+          // the range from slot q0 (in x cell ca, image m of the row) to q1
+          auto set_range = [&](int q0, int q1, int ca, int m, int& sr, int& lr, int& e0r,
+                               int& e1r, float& xbr, unsigned& hwr) {
+            const int dc = ca + m * nx - cx;
+            sr = q0;
+            lr = max(q1 - q0, 0);
+            e0r = cstart[rowbase + ca + 1];
+            e1r = ca + 2 <= nx ? cstart[rowbase + ca + 2] : 0x7fffffff;
+            xbr = (-static_cast<float>(dc) * wx - sxr) + xi;
+            hwr = hiw + static_cast<unsigned>(dc + kDcxBias);
+          };
+          // window [X0, X1) in unwrapped row coordinates (image m0); the own
+          // row starts right after slot k
+          float X0 = xa, X1 = xa + A.rc + 1e-5f;
+          int m0 = 0;
+          if (row != 0) {
+            const float w = sqrtf(w2) + 1e-5f;
+            float cc = xa - sxr;  // in (-lenx, 2 lenx)
+            if (cc < 0.f) { cc += lenx; m0 = -1; }
+            else if (cc >= lenx) { cc -= lenx; m0 = 1; }
+            X0 = cc - w;
+            X1 = cc + w;
           }
+          const bool wl = X0 < 0.f, wh = X1 > lenx, wrap = wl || wh;
+          int c0 = cx, c1;
+          const int q0 = (row == 0) ? k + 1 : lower(wl ? X0 + lenx : X0, c0);
+          const int q1 = lower(wh ? X1 - lenx : X1, c1);
+          const int rowstart = cstart[rowbase], rowend = cstart[rowbase + nx];
+          set_range(q0, wrap ? rowend : q1, c0, wl ? m0 - 1 : m0, s1, len1, e01, e11, xb1, hw1);
+          set_range(rowstart, wrap ? q1 : rowstart, 0, wl ? m0 : m0 + 1, s2, len2, e02, e12,
+                    xb2, hw2);
         }
         const int len = len1 + len2;
         const int lmax = __reduce_max_sync(FULL, len);
