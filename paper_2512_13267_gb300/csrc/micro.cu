@@ -558,42 +558,46 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
         const float yb = -static_cast<float>(dy) * wy + yi, zb = -static_cast<float>(dz) * wz + zi;
         const unsigned lo_i = static_cast<unsigned>(i);
         const int s2o = s2 - len1;
-        for (int t = 0; t < lmax; ++t) {
-          bool hit = false;
-          unsigned lo_w = 0u, hi_w = 0u;
-          if (t < len) {
-            const bool first = t < len1;
-            const int q = t + (first ? s1 : s2o);
-            const bool p0 = q >= (first ? e01 : e02), p1 = q >= (first ? e11 : e12);
-            float bx = first ? xb1 : xb2;
-            bx = p0 ? bx - wx : bx;
-            bx = p1 ? bx - wx : bx;
-            const int j = perm[q];
-            const float rx = bx - ox[j];
-            const float ry = yb - oy[j];
-            const float rz = zb - oz[j];
-            const float r2 = rx * rx + ry * ry + rz * rz;
-            hit = (r2 < A.rc2) && (r2 > 0.f);
-            if (hit && !A.dpd_on_bonded) {
-              const int lo = min(i, j), hi = max(i, j);
-              if (hi == lo + 1 && hi < sB.n_poly && (hi % A.chain_len) != 0) hit = false;
+        // fill the warp's queue from the slot windows; whenever it holds 32
+        // pairs, leave the (register-light) fill loop to evaluate them
+        int t = 0;
+        while (true) {
+          for (; t < lmax && count < 32; ++t) {
+            bool hit = false;
+            unsigned lo_w = 0u, hi_w = 0u;
+            if (t < len) {
+              const bool first = t < len1;
+              const int q = t + (first ? s1 : s2o);
+              const bool p0 = q >= (first ? e01 : e02), p1 = q >= (first ? e11 : e12);
+              float bx = first ? xb1 : xb2;
+              bx = p0 ? bx - wx : bx;
+              bx = p1 ? bx - wx : bx;
+              const int j = perm[q];
+              const float rx = bx - ox[j];
+              const float ry = yb - oy[j];
+              const float rz = zb - oz[j];
+              const float r2 = rx * rx + ry * ry + rz * rz;
+              hit = (r2 < A.rc2) && (r2 > 0.f);
+              if (hit && !A.dpd_on_bonded) {
+                const int lo = min(i, j), hi = max(i, j);
+                if (hi == lo + 1 && hi < sB.n_poly && (hi % A.chain_len) != 0) hit = false;
+              }
+              lo_w = lo_i | (static_cast<unsigned>(j) << 16);
+              hi_w = (first ? hw1 : hw2) + static_cast<unsigned>(p0) + static_cast<unsigned>(p1);
             }
-            lo_w = lo_i | (static_cast<unsigned>(j) << 16);
-            hi_w = (first ? hw1 : hw2) + static_cast<unsigned>(p0) + static_cast<unsigned>(p1);
+            const unsigned bal = __ballot_sync(FULL, hit);
+            if (hit)
+              queue[count + __popc(bal & lt_mask)] =
+                  (static_cast<unsigned long long>(hi_w) << 32) | lo_w;
+            count += __popc(bal);
           }
-          const unsigned bal = __ballot_sync(FULL, hit);
-          if (hit)
-            queue[count + __popc(bal & lt_mask)] =
-                (static_cast<unsigned long long>(hi_w) << 32) | lo_w;
-          count += __popc(bal);
-          if (count >= 32) {
-            __syncwarp();
-            eval_pair(queue[lane]);
-            __syncwarp();
-            if (lane < count - 32) queue[lane] = queue[32 + lane];
-            __syncwarp();
-            count -= 32;
-          }
+          if (count < 32) break;
+          __syncwarp();
+          eval_pair(queue[lane]);
+          __syncwarp();
+          if (lane < count - 32) queue[lane] = queue[32 + lane];
+          __syncwarp();
+          count -= 32;
         }
       }
     }

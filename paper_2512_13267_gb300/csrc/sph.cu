@@ -10,8 +10,10 @@
 // -(pi_I/d_I^2 + pi_J/d_J^2) F_IJ r_IJ, plus the body force; then the second
 // half kick.  After the substeps the velocity gradient of every fluid
 // particle, L_ab = dv_a/dx_b = sum_J (F_IJ/d_J) v_IJ,a r_IJ,b, is exported as
-// a 3x3 tensor for its micro-domain.  One thread per particle; every sum runs
-// in a fixed neighbour order, so a step is bit-reproducible.
+// a 3x3 tensor for its micro-domain.  A group of kGroup lanes shares one
+// particle: each lane takes every kGroup-th slot of the 3x3 neighbour cells
+// in a fixed order, and the group adds its partial sums with a fixed
+// butterfly, so a step is bit-reproducible.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -86,19 +88,21 @@ __global__ void sph_kick_drift(SphArgs A, float half_dt, int drift) {
   }
 }
 
-// counting sort by cell in one block: count, scan, scatter, then ascending
-// particle order inside each cell
-__global__ void sph_cells(SphArgs A) {
+// Counting sort by cell in four launches: bin and count (cnt must be zero on
+// entry), exclusive scan in one block (which clears cnt for use as cursors),
+// scatter, and an ascending-index sort inside each cell, which leaves cnt zero
+// again for the next build.
+__global__ void sph_bin(SphArgs A) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= A.n) return;
+  const int c = cell_index(A.pos[I], A);
+  A.cell_of[I] = c;
+  atomicAdd(&A.cnt[c], 1);
+}
+
+__global__ void sph_scan(SphArgs A) {
   __shared__ int warp_tot[32];
   const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
-  for (int c = tid; c < A.ncell; c += T) A.cnt[c] = 0;
-  __syncthreads();
-  for (int I = tid; I < A.n; I += T) {
-    const int c = cell_index(A.pos[I], A);
-    A.cell_of[I] = c;
-    atomicAdd(&A.cnt[c], 1);
-  }
-  __syncthreads();
   const int per = (A.ncell + T - 1) / T;
   const int c0 = min(tid * per, A.ncell), c1 = min(c0 + per, A.ncell);
   int local = 0;
@@ -127,15 +131,31 @@ __global__ void sph_cells(SphArgs A) {
     A.cnt[c] = 0;
   }
   if (tid == 0) A.start[A.ncell] = A.n;
-  __syncthreads();
-  for (int I = tid; I < A.n; I += T) {
-    const int c = A.cell_of[I];
-    A.perm[A.start[c] + atomicAdd(&A.cnt[c], 1)] = I;
-  }
-  __syncthreads();
-  for (int c = tid; c < A.ncell; c += T) {
-    const int s0 = A.start[c], s1 = A.start[c + 1];
-    for (int q = s0 + 1; q < s1; ++q) {
+}
+
+__global__ void sph_scatter(SphArgs A) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= A.n) return;
+  const int c = A.cell_of[I];
+  A.perm[A.start[c] + atomicAdd(&A.cnt[c], 1)] = I;
+}
+
+// One warp per cell: a cell of up to 32 particles is ranked with shuffles
+// (rank = number of smaller indices) and written back in ascending order;
+// larger cells (far denser than any SPH state) fall back to an insertion
+// sort by lane 0.
+__global__ void sph_cellsort(SphArgs A) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (c >= A.ncell) return;  // whole warp
+  const int s0 = A.start[c], m = A.start[c + 1] - s0;
+  if (m <= 32) {
+    const int key = lane < m ? A.perm[s0 + lane] : 0x7fffffff;
+    int rank = 0;
+    for (int t = 0; t < m; ++t) rank += __shfl_sync(0xffffffffu, key, t) < key;
+    __syncwarp();
+    if (lane < m) A.perm[s0 + rank] = key;
+  } else if (lane == 0) {
+    for (int q = s0 + 1; q < s0 + m; ++q) {
       const int key = A.perm[q];
       int k = q - 1;
       while (k >= s0 && A.perm[k] > key) {
@@ -145,11 +165,15 @@ __global__ void sph_cells(SphArgs A) {
       A.perm[k + 1] = key;
     }
   }
+  if (lane == 0) A.cnt[c] = 0;
 }
 
-// visits the 3x3 cell neighbourhood of particle I in a fixed order
+constexpr int kGroup = 8;  // lanes per particle in the neighbour sums
+
+// Visits lane g's share of the 3x3 cell neighbourhood of particle I: the
+// cells in a fixed order, every kGroup-th slot of each starting at g.
 template <typename F>
-__device__ __forceinline__ void for_neighbours(const SphArgs& A, int I, F&& fn) {
+__device__ __forceinline__ void for_neighbours(const SphArgs& A, int I, int g, F&& fn) {
   const int c = A.cell_of[I];
   const int cx = c % A.ncx, cy = c / A.ncx;
   for (int dy = -1; dy <= 1; ++dy) {
@@ -162,104 +186,150 @@ __device__ __forceinline__ void for_neighbours(const SphArgs& A, int I, F&& fn) 
       x -= (x >= A.ncx) ? A.ncx : 0;
       const int cc = x + A.ncx * y;
       const int e = A.start[cc + 1];
-      for (int q = A.start[cc]; q < e; ++q) fn(A.perm[q]);
+      for (int q = A.start[cc] + g; q < e; q += kGroup) fn(A.perm[q]);
     }
   }
+}
+
+// Sum over the kGroup lanes of a group (every lane of the warp takes part;
+// a + b == b + a exactly, so every lane of the group gets the same bits).
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+  for (int o = kGroup / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
 __global__ void sph_density(SphArgs A) {
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  if (I >= A.n) return;
-  const float2 ri = A.pos[I];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int I = t / kGroup, g = t % kGroup;
+  const bool valid = I < A.n;
   float s = 0.f;
-  for_neighbours(A, I, [&](int J) {
-    const float2 r = min_image(ri, A.pos[J], A.Lx, A.Ly);
-    s += kernel_W(A.kernel, sqrtf(r.x * r.x + r.y * r.y), A.h, A.hinv);
-  });
-  A.d[I] = s;
-  const float rr = A.mass * s / A.rho0;
-  const float r2 = rr * rr, r4 = r2 * r2;
-  A.p[I] = A.c2rho0_7 * (r4 * r2 * rr - 1.f) + A.pb;  // Eq. tait
+  if (valid) {
+    const float2 ri = A.pos[I];
+    for_neighbours(A, I, g, [&](int J) {
+      const float2 r = min_image(ri, A.pos[J], A.Lx, A.Ly);
+      s += kernel_W(A.kernel, sqrtf(r.x * r.x + r.y * r.y), A.h, A.hinv);
+    });
+  }
+  s = group_sum(s);
+  if (valid && g == 0) {
+    A.d[I] = s;
+    const float rr = A.mass * s / A.rho0;
+    const float r2 = rr * rr, r4 = r2 * r2;
+    A.p[I] = A.c2rho0_7 * (r4 * r2 * rr - 1.f) + A.pb;  // Eq. tait
+  }
 }
 
 __global__ void sph_force(SphArgs A, const double* stress) {
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  if (I >= A.n) return;
-  if (A.wall[I]) {
-    A.acc[I] = make_float2(0.f, 0.f);
-    return;
-  }
-  const float2 ri = A.pos[I], vi = A.vel[I];
-  const float di = A.d[I], pi_ = A.p[I];
-  const float Pi = pi_ / (di * di);
-  float sxx = 0.f, sxy = 0.f, syy = 0.f;
-  if (stress && I < A.n_fluid) {
-    const float inv = 1.f / (di * di);
-    sxx = static_cast<float>(stress[6 * I + 0]) * inv;
-    syy = static_cast<float>(stress[6 * I + 1]) * inv;
-    sxy = static_cast<float>(stress[6 * I + 3]) * inv;
-  }
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int I = t / kGroup, g = t % kGroup;
+  const bool active = I < A.n && !A.wall[I];
   float fx = 0.f, fy = 0.f;
-  for_neighbours(A, I, [&](int J) {
-    if (J == I) return;
-    const float2 r = min_image(ri, A.pos[J], A.Lx, A.Ly);
-    const float rr = sqrtf(r.x * r.x + r.y * r.y);
-    const float F = kernel_F(A.kernel, rr, A.hinv);
-    if (F == 0.f || rr == 0.f) return;  // e_IJ undefined for coincident particles
-    const float dj = A.d[J];
-    const float P = Pi + A.p[J] / (dj * dj);
-    fx += P * F * r.x;
-    fy += P * F * r.y;
-    const float2 vj = A.vel[J];
-    const float vx = vi.x - vj.x, vy = vi.y - vj.y;
-    const float inv_r = 1.f / rr;
-    const float ex = r.x * inv_r, ey = r.y * inv_r;
-    const float ve = vx * ex + vy * ey;
-    const float cv = F / (di * dj);
-    fx -= (A.a_visc * vx + A.b_visc * ve * ex) * cv;
-    fy -= (A.a_visc * vy + A.b_visc * ve * ey) * cv;
-    if (stress) {
-      float jxx = sxx, jxy = sxy, jyy = syy;
-      if (J < A.n_fluid && !A.wall[J]) {
-        const float inv = 1.f / (dj * dj);
-        jxx += static_cast<float>(stress[6 * J + 0]) * inv;
-        jyy += static_cast<float>(stress[6 * J + 1]) * inv;
-        jxy += static_cast<float>(stress[6 * J + 3]) * inv;
-      }
-      fx -= (jxx * r.x + jxy * r.y) * F;
-      fy -= (jxy * r.x + jyy * r.y) * F;
+  float2 ri = make_float2(0.f, 0.f);
+  if (active) {
+    ri = A.pos[I];
+    const float2 vi = A.vel[I];
+    const float di = A.d[I], pi_ = A.p[I];
+    const float Pi = pi_ / (di * di);
+    float sxx = 0.f, sxy = 0.f, syy = 0.f;
+    if (stress && I < A.n_fluid) {
+      const float inv = 1.f / (di * di);
+      sxx = static_cast<float>(stress[6 * I + 0]) * inv;
+      syy = static_cast<float>(stress[6 * I + 1]) * inv;
+      sxy = static_cast<float>(stress[6 * I + 3]) * inv;
     }
-  });
-  float gx = A.bfx, gy = A.bfy;
-  if (A.body_mode == LHMM_SPH_BODY_REVERSE_POISEUILLE) {
-    gx = (ri.y >= 0.5f * A.Ly) ? A.bfx : -A.bfx;
-    gy = 0.f;
+    for_neighbours(A, I, g, [&](int J) {
+      if (J == I) return;
+      const float2 r = min_image(ri, A.pos[J], A.Lx, A.Ly);
+      const float rr = sqrtf(r.x * r.x + r.y * r.y);
+      const float F = kernel_F(A.kernel, rr, A.hinv);
+      if (F == 0.f || rr == 0.f) return;  // e_IJ undefined for coincident particles
+      const float dj = A.d[J];
+      const float P = Pi + A.p[J] / (dj * dj);
+      fx += P * F * r.x;
+      fy += P * F * r.y;
+      const float2 vj = A.vel[J];
+      const float vx = vi.x - vj.x, vy = vi.y - vj.y;
+      const float inv_r = 1.f / rr;
+      const float ex = r.x * inv_r, ey = r.y * inv_r;
+      const float ve = vx * ex + vy * ey;
+      const float cv = F / (di * dj);
+      fx -= (A.a_visc * vx + A.b_visc * ve * ex) * cv;
+      fy -= (A.a_visc * vy + A.b_visc * ve * ey) * cv;
+      if (stress) {
+        float jxx = sxx, jxy = sxy, jyy = syy;
+        if (J < A.n_fluid && !A.wall[J]) {
+          const float inv = 1.f / (dj * dj);
+          jxx += static_cast<float>(stress[6 * J + 0]) * inv;
+          jyy += static_cast<float>(stress[6 * J + 1]) * inv;
+          jxy += static_cast<float>(stress[6 * J + 3]) * inv;
+        }
+        fx -= (jxx * r.x + jxy * r.y) * F;
+        fy -= (jxy * r.x + jyy * r.y) * F;
+      }
+    });
   }
-  A.acc[I] = make_float2(fx / A.mass + gx, fy / A.mass + gy);
+  fx = group_sum(fx);
+  fy = group_sum(fy);
+  if (I < A.n && g == 0) {
+    if (!active) {
+      A.acc[I] = make_float2(0.f, 0.f);  // wall particles stay fixed
+    } else {
+      float gx = A.bfx, gy = A.bfy;
+      if (A.body_mode == LHMM_SPH_BODY_REVERSE_POISEUILLE) {
+        gx = (ri.y >= 0.5f * A.Ly) ? A.bfx : -A.bfx;
+        gy = 0.f;
+      }
+      A.acc[I] = make_float2(fx / A.mass + gx, fy / A.mass + gy);
+    }
+  }
 }
 
 __global__ void sph_velgrad(SphArgs A, float* L_out) {
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  if (I >= A.n_fluid) return;
-  const float2 ri = A.pos[I], vi = A.vel[I];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int I = t / kGroup, g = t % kGroup;
+  const bool valid = I < A.n_fluid;
   float Lxx = 0.f, Lxy = 0.f, Lyx = 0.f, Lyy = 0.f;
-  for_neighbours(A, I, [&](int J) {
-    if (J == I) return;
-    const float2 r = min_image(ri, A.pos[J], A.Lx, A.Ly);
-    const float F = kernel_F(A.kernel, sqrtf(r.x * r.x + r.y * r.y), A.hinv);
-    if (F == 0.f) return;
-    const float2 vj = A.vel[J];
-    const float cf = F / A.d[J];
-    const float vx = vi.x - vj.x, vy = vi.y - vj.y;
-    Lxx += cf * vx * r.x;
-    Lxy += cf * vx * r.y;
-    Lyx += cf * vy * r.x;
-    Lyy += cf * vy * r.y;
-  });
-  float* o = L_out + 9 * I;
-  o[0] = Lxx; o[1] = Lxy; o[2] = 0.f;
-  o[3] = Lyx; o[4] = Lyy; o[5] = 0.f;
-  o[6] = 0.f; o[7] = 0.f; o[8] = 0.f;
+  if (valid) {
+    const float2 ri = A.pos[I], vi = A.vel[I];
+    for_neighbours(A, I, g, [&](int J) {
+      if (J == I) return;
+      const float2 r = min_image(ri, A.pos[J], A.Lx, A.Ly);
+      const float F = kernel_F(A.kernel, sqrtf(r.x * r.x + r.y * r.y), A.hinv);
+      if (F == 0.f) return;
+      const float2 vj = A.vel[J];
+      const float cf = F / A.d[J];
+      const float vx = vi.x - vj.x, vy = vi.y - vj.y;
+      Lxx += cf * vx * r.x;
+      Lxy += cf * vx * r.y;
+      Lyx += cf * vy * r.x;
+      Lyy += cf * vy * r.y;
+    });
+  }
+  Lxx = group_sum(Lxx);
+  Lxy = group_sum(Lxy);
+  Lyx = group_sum(Lyx);
+  Lyy = group_sum(Lyy);
+  if (valid && g == 0) {
+    float* o = L_out + 9 * I;
+    o[0] = Lxx; o[1] = Lxy; o[2] = 0.f;
+    o[3] = Lyx; o[4] = Lyy; o[5] = 0.f;
+    o[6] = 0.f; o[7] = 0.f; o[8] = 0.f;
+  }
+}
+
+// grid for one group of kGroup lanes per item
+inline int group_grid(int n_items, int threads) {
+  return static_cast<int>((static_cast<long long>(n_items) * kGroup + threads - 1) / threads);
+}
+
+// cell list of the current positions (cnt is zero on entry and on exit)
+void build_cells(const SphArgs& a, cudaStream_t s) {
+  const int T = 128;
+  sph_bin<<<(a.n + T - 1) / T, T, 0, s>>>(a);
+  sph_scan<<<1, 1024, 0, s>>>(a);
+  sph_scatter<<<(a.n + T - 1) / T, T, 0, s>>>(a);
+  sph_cellsort<<<static_cast<int>((32LL * a.ncell + T - 1) / T), T, 0, s>>>(a);
 }
 
 }  // namespace
@@ -289,10 +359,10 @@ void free_sph(lhmm_sph_t h) {
 }
 
 cudaError_t eval_forces(lhmm_sph_s* h, const double* stress, cudaStream_t s) {
-  const int T = h->threads, G = (h->a.n + T - 1) / T;
-  sph_cells<<<1, 1024, 0, s>>>(h->a);
-  sph_density<<<G, T, 0, s>>>(h->a);
-  sph_force<<<G, T, 0, s>>>(h->a, stress);
+  const int T = h->threads, Gg = group_grid(h->a.n, T);
+  build_cells(h->a, s);
+  sph_density<<<Gg, T, 0, s>>>(h->a);
+  sph_force<<<Gg, T, 0, s>>>(h->a, stress);
   return cudaGetLastError();
 }
 
@@ -366,6 +436,7 @@ extern "C" lhmm_status lhmm_sph_create(const lhmm_sph_params* params, const floa
   if ((e = cudaMemcpyAsync(a.pos, pos.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(a.vel, vel.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(wall_d, wall.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(a.cnt, 0, sizeof(int) * a.ncell, s)) != cudaSuccess ||
       (e = eval_forces(h, nullptr, s)) != cudaSuccess || (e = cudaStreamSynchronize(s)) != cudaSuccess) {
     free_sph(h);
     return lhmm_cuda_error(e);
@@ -394,10 +465,10 @@ extern "C" lhmm_status lhmm_sph_step(lhmm_sph_t h, const double* stress_dev, int
   }
   if (L_out_dev) {
     if (n_substeps == 0) {  // density of the current positions
-      sph_cells<<<1, 1024, 0, s>>>(h->a);
-      sph_density<<<G, T, 0, s>>>(h->a);
+      build_cells(h->a, s);
+      sph_density<<<group_grid(h->a.n, T), T, 0, s>>>(h->a);
     }
-    const int Gf = (h->a.n_fluid + T - 1) / T;
+    const int Gf = group_grid(h->a.n_fluid, T);
     if (Gf > 0) sph_velgrad<<<Gf, T, 0, s>>>(h->a, L_out_dev);
   }
   LHMM_CK(cudaGetLastError());
@@ -520,11 +591,12 @@ extern "C" lhmm_status lhmm_sph_velgrad_noalloc(const lhmm_sph_params* params,
   a.perm = ib + kNoallocMaxParticles;
   a.d = reinterpret_cast<float*>(ib + 2 * kNoallocMaxParticles);
   a.p = reinterpret_cast<float*>(ib + 3 * kNoallocMaxParticles);
-  a.cnt = ib + 4 * kNoallocMaxParticles;  // cleared by sph_cells on every call
+  a.cnt = ib + 4 * kNoallocMaxParticles;  // zeroed at the start of every call
   a.start = a.cnt + kNoallocMaxCells;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int T = 128, G = (a.n + T - 1) / T, Gf = (a.n_fluid + T - 1) / T;
-  sph_cells<<<1, 1024, 0, s>>>(a);
+  const int T = 128, G = group_grid(a.n, T), Gf = group_grid(a.n_fluid, T);
+  LHMM_CK(cudaMemsetAsync(a.cnt, 0, sizeof(int) * a.ncell, s));
+  build_cells(a, s);
   sph_density<<<G, T, 0, s>>>(a);
   if (Gf > 0) sph_velgrad<<<Gf, T, 0, s>>>(a, L_out_dev);
   LHMM_CK(cudaGetLastError());
