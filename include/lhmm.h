@@ -354,6 +354,18 @@ lhmm_status lhmm_closure_info(lhmm_closure_t c, int64_t* n_params_per_member, in
 lhmm_status lhmm_coupled_set_closure(lhmm_coupled_t c, lhmm_closure_t closure, float threshold,
                                      float stress_floor, int audit_every);
 lhmm_status lhmm_coupled_enable_gate(lhmm_coupled_t c, int enabled);
+/* Change the gate's threshold, audit period and target without touching its
+ * state (gradient history, counters); threshold and audit_every follow the
+ * rules of set_closure.  absolute = 0: the closure predicts the increment of
+ * (pi_xx, pi_xy, pi_yy) over the macro step and a trusted particle takes
+ * pi += prediction (the set_closure default); absolute = 1: the closure
+ * predicts the stress itself from the gradient history alone (the three
+ * stress inputs are written as zero), a trusted particle takes pi =
+ * prediction, and the relative spread is taken against the predicted stress.
+ * Other values return LHMM_ERR_ARG.  The next macro step re-captures its
+ * graph.  Synchronous. */
+lhmm_status lhmm_coupled_set_gate(lhmm_coupled_t c, float threshold, int audit_every,
+                                  int absolute);
 /* Counters since the closure was attached: gated macro steps, boxes advanced
  * by DPD in them, audited boxes, and over the audited boxes the summed squared
  * error of the predicted increment and the summed squared DPD increment.

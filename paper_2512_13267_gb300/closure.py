@@ -19,10 +19,12 @@ HIST = 16
 STRESS_COLS = [0, 3, 1]  # xx, xy, yy in the micro stress layout
 
 
-def collect_pairs(coupled, n_steps, skip=HIST):
+def collect_pairs(coupled, n_steps, skip=HIST, absolute=False):
     """Run n_steps plain macro steps (gate off, closure attached) and return
-    inputs X (m x 67) and targets T (m x 3); the first `skip` steps only fill
-    the gradient history."""
+    inputs X (m x 67) and targets T (m x 3): the increment of (pi_xx, pi_xy,
+    pi_yy) over the step, or with `absolute` the stress after it (the gate
+    must be in its absolute mode, so that the stress inputs are zero); the
+    first `skip` steps only fill the gradient history."""
     coupled.enable_gate(False)
     Xs, Ts = [], []
     for k in range(n_steps):
@@ -31,7 +33,9 @@ def collect_pairs(coupled, n_steps, skip=HIST):
             continue
         X = coupled.closure_inputs()
         _, st = coupled.exchange()
-        T = st[:, STRESS_COLS].astype(np.float32) - X[:, 64:67]
+        T = st[:, STRESS_COLS].astype(np.float32)
+        if not absolute:
+            T = T - X[:, 64:67]
         Xs.append(X)
         Ts.append(T)
     if not Xs:
@@ -123,22 +127,38 @@ def _rate(cpl, steps):
 def surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, batch=4096, n_eval=60,
                        threshold=0.02, audit_every=50, timing_steps=10, seed=3, alpha=0.01,
                        U_o=0.25, c_factor=10.0, eta_s=0.1, k_micro=50, dt_dpd=0.01, members=5,
-                       lr=1e-3, weight_decay=1e-4, cosine=False, nbins=16):
+                       lr=1e-3, weight_decay=1e-4, cosine=False, nbins=16, thresholds=None,
+                       noise_floor=False, absolute=False):
     """Plain LHMM vs surrogate-gated LHMM on the coupled reverse-Poiseuille
     channel.  Two identical systems run the same `warm + n_data` plain steps
     (one collects training pairs); the ensemble trains on the GPU; then both run
     `n_eval` steps (plain vs gated) and the time-averaged y-binned pi_xy and N1
-    profiles are compared.  Returns a dict of rates, errors and counts."""
-    kw = dict(seed=seed, alpha=alpha, U_o=U_o, c_factor=c_factor, eta_s=eta_s, k_micro=k_micro,
+    profiles are compared.  `thresholds` (a list) runs one evaluation window of
+    `n_eval` steps per gate threshold, in order, each compared with the same
+    window of the plain run.  `noise_floor` adds a third, plain system with
+    another DPD seed and reports its profile error against the plain run over
+    the same windows: the error two plain runs already differ by.  Returns a
+    dict of rates, errors and counts.  `absolute` trains and gates the
+    closure on the stress itself from the gradient history (no stress input)
+    instead of the increment."""
+    kw = dict(alpha=alpha, U_o=U_o, c_factor=c_factor, eta_s=eta_s, k_micro=k_micro,
               dt_dpd=dt_dpd, members=members)
-    A, clo_a, cfg, M = _channel(closure_seed=1, **kw)
-    B, clo_b, _, _ = _channel(closure_seed=7, **kw)
+    A, clo_a, cfg, M = _channel(seed=seed, closure_seed=1, **kw)
+    B, clo_b, _, _ = _channel(seed=seed, closure_seed=7, **kw)
+    systems = [("A", A), ("B", B)]
+    C = None
+    if noise_floor:
+        C, clo_c, _, _ = _channel(seed=seed + 1000, closure_seed=1, **kw)
+        systems.append(("C", C))
     A.set_closure(clo_a, threshold=threshold, audit_every=audit_every)
     B.set_closure(clo_b, threshold=threshold, audit_every=audit_every)
+    B.set_gate(threshold, audit_every, absolute)
     t0 = time.perf_counter()
     A.step(warm + n_data, use_graph=True)
+    if C is not None:
+        C.step(warm + n_data, use_graph=True)
     B.step(warm, use_graph=True)
-    X, T = collect_pairs(B, n_data, skip=0)
+    X, T = collect_pairs(B, n_data, skip=0, absolute=absolute)
     t_data = time.perf_counter() - t0
     mean, std, scale = normalization(X, T)
     clo_b.set_normalization(mean, std, scale)
@@ -147,27 +167,43 @@ def surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, batch=4096, n_eval
                           cosine=cosine)
     B.enable_gate(True)
     Ly = cfg["Ly"]
-    acc = {"A": [np.zeros(nbins), np.zeros(nbins)], "B": [np.zeros(nbins), np.zeros(nbins)]}
-    for _ in range(n_eval):
-        for name, sysm in (("A", A), ("B", B)):
-            sysm.step(1, use_graph=True)
-            y = sysm.sph.get_state()[0][:, 1]
-            _, st = sysm.exchange()
-            pxy, n1 = binned_profiles(y, st, Ly, nbins)
-            acc[name][0] += pxy / n_eval
-            acc[name][1] += n1 / n_eval
+    windows = []
+    for thr in (thresholds if thresholds else [threshold]):
+        B.set_gate(thr, audit_every, absolute)
+        acc = {name: [np.zeros(nbins), np.zeros(nbins)] for name, _ in systems}
+        g_before = B.gate_stats()
+        for _ in range(n_eval):
+            for name, sysm in systems:
+                sysm.step(1, use_graph=True)
+                y = sysm.sph.get_state()[0][:, 1]
+                _, st = sysm.exchange()
+                pxy, n1 = binned_profiles(y, st, Ly, nbins)
+                acc[name][0] += pxy / n_eval
+                acc[name][1] += n1 / n_eval
+        g_after = B.gate_stats()
+        w = dict(threshold=thr,
+                 stress_error_pxy=rel_l2(acc["B"][0], acc["A"][0]),
+                 stress_error_n1=rel_l2(acc["B"][1], acc["A"][1]),
+                 dpd_fraction=(g_after["dpd_boxes"] - g_before["dpd_boxes"])
+                 / max(1, (g_after["gated_steps"] - g_before["gated_steps"]) * B.n_boxes),
+                 profile_pxy_plain=acc["A"][0].tolist(),
+                 profile_pxy_surrogate=acc["B"][0].tolist())
+        if C is not None:
+            w["noise_floor_pxy"] = rel_l2(acc["C"][0], acc["A"][0])
+            w["noise_floor_n1"] = rel_l2(acc["C"][1], acc["A"][1])
+        windows.append(w)
     gs0 = B.gate_stats()
     rate_plain = _rate(A, timing_steps)
     rate_gated = _rate(B, timing_steps)
     gs = B.gate_stats()
     status = [lhmm.status_string(x.micro.sync(raise_on_error=False)[0]) for x in (A, B)]
+    last = windows[-1]
     out = dict(
         device_status_plain=status[0], device_status_surrogate=status[1],
         macro_steps_per_s_plain=rate_plain, macro_steps_per_s_surrogate=rate_gated,
         speedup=rate_gated / rate_plain,
-        stress_error_pxy=rel_l2(acc["B"][0], acc["A"][0]),
-        stress_error_n1=rel_l2(acc["B"][1], acc["A"][1]),
-        dpd_fraction_eval=gs0["dpd_boxes"] / max(1, gs0["gated_steps"] * B.n_boxes),
+        stress_error_pxy=last["stress_error_pxy"], stress_error_n1=last["stress_error_n1"],
+        dpd_fraction_eval=last["dpd_fraction"],
         dpd_fraction_timed=(gs["dpd_boxes"] - gs0["dpd_boxes"])
         / max(1, (gs["gated_steps"] - gs0["gated_steps"]) * B.n_boxes),
         audit_rel_err=float(np.sqrt(gs["audit_err2"] / max(gs["audit_ref2"], 1e-300))),
@@ -175,9 +211,14 @@ def surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, batch=4096, n_eval
         train_loss_first=[float(x) for x in hist[0]] if hist else None,
         train_loss_last=[float(x) for x in hist[-1]] if hist else None,
         t_data_s=t_data, t_train_s=t_train, sph_substeps=M, micro_steps=k_micro,
-        boxes=B.n_boxes, threshold=threshold, audit_every=audit_every, n_eval=n_eval,
-        profile_pxy_plain=acc["A"][0].tolist(), profile_pxy_surrogate=acc["B"][0].tolist())
-    for obj in (A, B, clo_a, clo_b):
+        boxes=B.n_boxes, threshold=last["threshold"], audit_every=audit_every, n_eval=n_eval,
+        target="stress" if absolute else "increment",
+        windows=windows if len(windows) > 1 else None,
+        noise_floor_pxy=last.get("noise_floor_pxy"), noise_floor_n1=last.get("noise_floor_n1"),
+        profile_pxy_plain=last["profile_pxy_plain"],
+        profile_pxy_surrogate=last["profile_pxy_surrogate"])
+    objs = [A, B, clo_a, clo_b] + ([C, clo_c] if C is not None else [])
+    for obj in objs:
         obj.close()
     return out
 

@@ -19,6 +19,7 @@ struct GateState {
   float threshold = 0.02f;  // relative ensemble spread above which a box runs DPD
   float floor = 1e-3f;      // stress scale floor of the relative spread
   int audit_every = 50;     // every audit_every-th trusted box (round robin) runs DPD anyway
+  int absolute = 0;         // 0: closure predicts the increment of pi; 1: pi itself
   int enabled = 0;
   float* hist = nullptr;    // n x kHist x 4 ring of (Lxx, Lxy, Lyx, Lyy)
   float* X = nullptr;       // n x kFeat closure inputs
@@ -49,9 +50,10 @@ struct lhmm_coupled_s {
 namespace {
 
 // push this step's gradient into the ring and build the closure input
-// [L(t-15) .. L(t) as (Lxx, Lxy, Lyx, Lyy), pi_xx, pi_xy, pi_yy]
+// [L(t-15) .. L(t) as (Lxx, Lxy, Lyx, Lyy), pi_xx, pi_xy, pi_yy]; in the
+// absolute mode the stress entries are zero (the input is the history alone)
 __global__ void gate_features(const float* L, const double* stress, int n, float* hist,
-                              const long long* counters, float* X) {
+                              const long long* counters, float* X, int absolute) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= n) return;
   const int head = static_cast<int>(counters[3] % kHist);
@@ -67,26 +69,29 @@ __global__ void gate_features(const float* L, const double* stress, int n, float
     for (int q = 0; q < 4; ++q) x[4 * k + q] = h[4 * src + q];
   }
   const double* s = stress + 6 * static_cast<long long>(I);
-  x[4 * kHist + 0] = static_cast<float>(s[0]);
-  x[4 * kHist + 1] = static_cast<float>(s[3]);
-  x[4 * kHist + 2] = static_cast<float>(s[1]);
+  x[4 * kHist + 0] = absolute ? 0.f : static_cast<float>(s[0]);
+  x[4 * kHist + 1] = absolute ? 0.f : static_cast<float>(s[3]);
+  x[4 * kHist + 2] = absolute ? 0.f : static_cast<float>(s[1]);
 }
 
 __global__ void advance_ring(long long* counters) { counters[3] += 1; }
 
-// trust test and compaction; trusted boxes take the predicted increment,
+// trust test and compaction; trusted boxes take the prediction (pi += the
+// predicted increment, or pi = the predicted stress in the absolute mode),
 // the others (and an audit share of the trusted ones) go to the DPD list
 __global__ void gate_select(const float* mean, const float* spread, double* stress, int n,
-                            float thr, float floor_, int audit_every, long long* counters,
-                            int* active, int* n_active, unsigned char* audited, float* pred,
-                            float* before) {
+                            float thr, float floor_, int audit_every, int absolute,
+                            long long* counters, int* active, int* n_active,
+                            unsigned char* audited, float* pred, float* before) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= n) return;
   double* s = stress + 6 * static_cast<long long>(I);
   const float dxx = mean[3 * I], dxy = mean[3 * I + 1], dyy = mean[3 * I + 2];
   // scale: magnitude (Frobenius) of the predicted in-plane stress tensor
-  const float pxx = static_cast<float>(s[0]) + dxx, pxy = static_cast<float>(s[3]) + dxy,
-              pyy = static_cast<float>(s[1]) + dyy;
+  const float bxx = absolute ? 0.f : static_cast<float>(s[0]);
+  const float bxy = absolute ? 0.f : static_cast<float>(s[3]);
+  const float byy = absolute ? 0.f : static_cast<float>(s[1]);
+  const float pxx = bxx + dxx, pxy = bxy + dxy, pyy = byy + dyy;
   const float scale = fmaxf(sqrtf(pxx * pxx + 2.f * pxy * pxy + pyy * pyy), floor_);
   const bool trust = spread[I] <= thr * scale;
   const long long step = counters[0];
@@ -98,14 +103,14 @@ __global__ void gate_select(const float* mean, const float* spread, double* stre
       pred[3 * I] = dxx;
       pred[3 * I + 1] = dxy;
       pred[3 * I + 2] = dyy;
-      before[3 * I] = static_cast<float>(s[0]);
-      before[3 * I + 1] = static_cast<float>(s[3]);
-      before[3 * I + 2] = static_cast<float>(s[1]);
+      before[3 * I] = bxx;
+      before[3 * I + 1] = bxy;
+      before[3 * I + 2] = byy;
     }
   } else {
-    s[0] += dxx;
-    s[3] += dxy;
-    s[1] += dyy;
+    s[0] = static_cast<double>(bxx) + dxx;
+    s[3] = static_cast<double>(bxy) + dxy;
+    s[1] = static_cast<double>(byy) + dyy;
   }
 }
 
@@ -133,7 +138,7 @@ lhmm_status enqueue_macro_step(lhmm_coupled_s* c, cudaStream_t s, bool gated) {
   GateState& g = c->gate;
   const int n = c->n_boxes, T = 128, G = (n + T - 1) / T;
   if (g.closure) {
-    gate_features<<<G, T, 0, s>>>(c->L_d, c->stress_d, n, g.hist, g.counters, g.X);
+    gate_features<<<G, T, 0, s>>>(c->L_d, c->stress_d, n, g.hist, g.counters, g.X, g.absolute);
     advance_ring<<<1, 1, 0, s>>>(g.counters);
     LHMM_CK(cudaGetLastError());
   }
@@ -144,7 +149,8 @@ lhmm_status enqueue_macro_step(lhmm_coupled_s* c, cudaStream_t s, bool gated) {
   if (st != LHMM_OK) return st;
   LHMM_CK(cudaMemsetAsync(g.n_active, 0, sizeof(int), s));
   gate_select<<<G, T, 0, s>>>(g.mean, g.spread, c->stress_d, n, g.threshold, g.floor, g.audit_every,
-                              g.counters, g.active, g.n_active, g.audited, g.pred, g.before);
+                              g.absolute, g.counters, g.active, g.n_active, g.audited, g.pred,
+                              g.before);
   gate_tally<<<1, 1, 0, s>>>(g.counters, g.n_active);
   LHMM_CK(cudaGetLastError());
   st = lhmm_micro_advance_dev_count(c->micro, c->L_d, g.active, g.n_active, n, c->micro_steps,
@@ -305,6 +311,19 @@ extern "C" lhmm_status lhmm_coupled_set_closure(lhmm_coupled_t c, lhmm_closure_t
   g.floor = stress_floor;
   g.audit_every = audit_every;
   g.enabled = 0;
+  return LHMM_OK;
+}
+
+extern "C" lhmm_status lhmm_coupled_set_gate(lhmm_coupled_t c, float threshold, int audit_every,
+                                             int absolute) {
+  if (!c || !c->gate.closure || !(threshold >= 0.f) || audit_every < 0 ||
+      (absolute != 0 && absolute != 1))
+    return LHMM_ERR_ARG;
+  LHMM_CK(cudaDeviceSynchronize());
+  drop_graphs(c);  // the gate's launch arguments are baked into the captured graph
+  c->gate.threshold = threshold;
+  c->gate.audit_every = audit_every;
+  c->gate.absolute = absolute;
   return LHMM_OK;
 }
 

@@ -502,21 +502,25 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
                                (static_cast<unsigned>(ikm) << 12) |
                                (static_cast<unsigned>(cross) << 14);
           const int rowbase = nx * (y + ny * z);
-          // first slot of the row with x >= X (X in [0, lenx]; binary search
-          // inside the cell that holds X), and that cell
+          // first slot of the row with x >= X (X in [0, lenx]) and the cell
+          // that holds X: inside the cell (sorted by x) the length of the
+          // prefix with x < X is built from steps of 8, 4, 2, 1 (exact up to
+          // 15 beads), then extended one by one (only in cells of more)
           auto lower = [&](float X, int& cell) -> int {
             const int c = min(__float2int_rd(X * winvx), nx - 1);
             const float xr = X - static_cast<float>(c) * wx;
             int lo = cstart[rowbase + c];
             int n = cstart[rowbase + c + 1] - lo;
-            while (n > 0) {
-              const int half = n >> 1;
-              if (ox[perm[lo + half]] < xr) {
-                lo += half + 1;
-                n -= half + 1;
-              } else {
-                n = half;
+#pragma unroll
+            for (int st = 8; st > 0; st >>= 1) {
+              if (st <= n && ox[perm[lo + st - 1]] < xr) {
+                lo += st;
+                n -= st;
               }
+            }
+            while (n > 0 && ox[perm[lo]] < xr) {
+              ++lo;
+              --n;
             }
             cell = c;
             return lo;
@@ -537,7 +541,7 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
           float X0 = xa, X1 = xa + A.rc + 1e-5f;
           int m0 = 0;
           if (row != 0) {
-            const float w = sqrtf(w2) + 1e-5f;
+            const float w = w2 * rsqrtf(w2) + 1e-5f;  // margin covers rsqrtf's error
             float cc = xa - sxr;  // in (-lenx, 2 lenx)
             if (cc < 0.f) { cc += lenx; m0 = -1; }
             else if (cc >= lenx) { cc -= lenx; m0 = 1; }

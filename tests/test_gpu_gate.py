@@ -98,3 +98,40 @@ def test_audit_share_runs_dpd_and_measures_error():
     assert st["gated_steps"] == 4
     assert st["dpd_boxes"] == st["audited"] == 4 * cpl.n_boxes // 4
     assert st["audit_ref2"] > 0 and st["audit_err2"] > 0
+
+
+def test_set_gate_keeps_history_and_switches_threshold():
+    cpl, clo = _system(seed=15)
+    cpl.set_closure(clo, threshold=1e30, audit_every=0)
+    cpl.step(17, use_graph=True)
+    X0 = cpl.closure_inputs()
+    cpl.set_gate(0.0, 0)
+    assert np.array_equal(cpl.closure_inputs(), X0)
+    cpl.enable_gate(True)
+    cpl.step(2, use_graph=True)
+    st = cpl.gate_stats()
+    assert st["gated_steps"] == 2 and st["dpd_boxes"] == 2 * cpl.n_boxes
+    cpl.set_gate(1e30, 0)
+    cpl.step(3, use_graph=True)  # eager, capture, replay with the new threshold
+    st2 = cpl.gate_stats()
+    assert st2["gated_steps"] == 5 and st2["dpd_boxes"] == st["dpd_boxes"]
+
+
+def test_absolute_mode_sets_stress_to_prediction():
+    cpl, clo = _system(seed=17)
+    cpl.set_closure(clo, threshold=1e30, audit_every=0)
+    cpl.set_gate(1e30, 0, absolute=True)
+    cpl.step(17, use_graph=True)
+    assert np.all(cpl.closure_inputs()[:, 64:67] == 0.0)
+    _, st0 = cpl.exchange()
+    cpl.enable_gate(True)
+    cpl.step(1, use_graph=False)
+    X = cpl.closure_inputs()
+    assert np.all(X[:, 64:67] == 0.0)
+    _, st1 = cpl.exchange()
+    mean = torch.zeros((cpl.n_boxes, 3), dtype=torch.float32, device="cuda")
+    spread = torch.zeros(cpl.n_boxes, dtype=torch.float32, device="cuda")
+    clo.infer(torch.from_numpy(X).cuda(), mean, spread)
+    assert np.allclose(st1[:, [0, 3, 1]], mean.cpu().numpy(), rtol=1e-6, atol=1e-9)
+    assert np.array_equal(st1[:, [2, 4, 5]], st0[:, [2, 4, 5]])
+    assert cpl.gate_stats()["dpd_boxes"] == 0
