@@ -87,7 +87,7 @@ constexpr int kRedFloats = 192;  // 6 x 32 warps, also scan scratch
 constexpr float kFixScale = 262144.f;
 constexpr float kFixInv = 1.f / 262144.f;
 constexpr float kFixMax = 512.f;
-constexpr int kQueue = 64;       // pair-queue entries per warp
+constexpr int kQueue = 65;       // pair-queue entries per warp (64 + a slot for misses)
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
@@ -477,15 +477,10 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
         unsigned hw1 = 0u, hw2 = 0u;  // upper word of the range's queue entries at dc
         const int z = wrapi(cz + dz, nz);
         int y = cy + dy;
-        int cross = 0;
-        float sxr = 0.f;
-        if (y < 0) {
-          y += ny;
-          if (le) { cross = 2; sxr = -le_off; }
-        } else if (y >= ny) {
-          y -= ny;
-          if (le) { cross = 1; sxr = le_off; }
-        }
+        const bool below = y < 0, above = y >= ny;
+        y += below ? ny : (above ? -ny : 0);
+        const int cross = !le ? 0 : (below ? 2 : (above ? 1 : 0));
+        const float sxr = !le ? 0.f : (below ? -le_off : (above ? le_off : 0.f));
         // Beads of the row's cell column within rc of i lie within |x_j - c|
         // < w of the (image-shifted) centre c = x_i - sxr, where w^2 = rc^2 -
         // ey^2 - ez^2 and ey, ez are i's distances to the column in y and z;
@@ -494,7 +489,10 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
         const float ey = dy > 0 ? wy - yi : (dy < 0 ? yi : 0.f);
         const float ez = dz > 0 ? wz - zi : 0.f;
         const float w2 = A.rc2 - ey * ey - ez * ez;
-        if (k < N && w2 > 0.f) {
+        // computed by every lane (no divergent branch); lanes without a
+        // window (past the last bead, or w^2 <= 0) get zero lengths at the end
+        const bool has_window = k < N && w2 > 0.f;
+        {
           const float lenx = sB.len[0], winvx = sB.winv[0];
           const float xa = static_cast<float>(cx) * wx + xi;
           const unsigned hiw = (static_cast<unsigned>(dy + 1) << 8) |
@@ -513,10 +511,10 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
             int n = cstart[rowbase + c + 1] - lo;
 #pragma unroll
             for (int st = 8; st > 0; st >>= 1) {
-              if (st <= n && ox[perm[lo + st - 1]] < xr) {
-                lo += st;
-                n -= st;
-              }
+              const bool ok = st <= n;  // probe inside the cell, else a valid dummy slot
+              const bool take = ok && ox[perm[ok ? lo + st - 1 : 0]] < xr;
+              lo += take ? st : 0;
+              n -= take ? st : 0;
             }
             while (n > 0 && ox[perm[lo]] < xr) {
               ++lo;
@@ -541,10 +539,12 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
           float X0 = xa, X1 = xa + A.rc + 1e-5f;
           int m0 = 0;
           if (row != 0) {
-            const float w = w2 * rsqrtf(w2) + 1e-5f;  // margin covers rsqrtf's error
+            const float w2s = has_window ? w2 : 1e-12f;
+            const float w = w2s * rsqrtf(w2s) + 1e-5f;  // margin covers rsqrtf's error
             float cc = xa - sxr;  // in (-lenx, 2 lenx)
-            if (cc < 0.f) { cc += lenx; m0 = -1; }
-            else if (cc >= lenx) { cc -= lenx; m0 = 1; }
+            const bool neg = cc < 0.f, big = cc >= lenx;
+            cc = neg ? cc + lenx : (big ? cc - lenx : cc);
+            m0 = neg ? -1 : (big ? 1 : 0);
             X0 = cc - w;
             X1 = cc + w;
           }
@@ -556,6 +556,8 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
           set_range(q0, wrap ? rowend : q1, c0, wl ? m0 - 1 : m0, s1, len1, e01, e11, xb1, hw1);
           set_range(rowstart, wrap ? q1 : rowstart, 0, wl ? m0 : m0 + 1, s2, len2, e02, e12,
                     xb2, hw2);
+          len1 = has_window ? len1 : 0;
+          len2 = has_window ? len2 : 0;
         }
         const int len = len1 + len2;
         const int lmax = __reduce_max_sync(FULL, len);
@@ -567,11 +569,12 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
         int t = 0;
         while (true) {
           for (; t < lmax && count < 32; ++t) {
-            bool hit = false;
-            unsigned lo_w = 0u, hi_w = 0u;
-            if (t < len) {
+            bool hit;
+            unsigned lo_w, hi_w;
+            {  // no divergent branch: lanes past their window test slot 0
+              const bool act = t < len;
               const bool first = t < len1;
-              const int q = t + (first ? s1 : s2o);
+              const int q = act ? t + (first ? s1 : s2o) : 0;
               const bool p0 = q >= (first ? e01 : e02), p1 = q >= (first ? e11 : e12);
               float bx = first ? xb1 : xb2;
               bx = p0 ? bx - wx : bx;
@@ -581,18 +584,19 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
               const float ry = yb - oy[j];
               const float rz = zb - oz[j];
               const float r2 = rx * rx + ry * ry + rz * rz;
-              hit = (r2 < A.rc2) && (r2 > 0.f);
-              if (hit && !A.dpd_on_bonded) {
+              hit = act && (r2 < A.rc2) && (r2 > 0.f);
+              if (!A.dpd_on_bonded) {  // uniform: bonded pairs skip DPD (reading R5 off)
                 const int lo = min(i, j), hi = max(i, j);
-                if (hi == lo + 1 && hi < sB.n_poly && (hi % A.chain_len) != 0) hit = false;
+                hit = hit && !(hi == lo + 1 && hi < sB.n_poly && (hi % A.chain_len) != 0);
               }
               lo_w = lo_i | (static_cast<unsigned>(j) << 16);
               hi_w = (first ? hw1 : hw2) + static_cast<unsigned>(p0) + static_cast<unsigned>(p1);
             }
             const unsigned bal = __ballot_sync(FULL, hit);
-            if (hit)
-              queue[count + __popc(bal & lt_mask)] =
-                  (static_cast<unsigned long long>(hi_w) << 32) | lo_w;
+            // every lane stores (no divergent branch): misses go to the spare
+            // last slot, which no entry ever occupies (count + 32 <= 63)
+            queue[hit ? count + __popc(bal & lt_mask) : kQueue - 1] =
+                (static_cast<unsigned long long>(hi_w) << 32) | lo_w;
             count += __popc(bal);
           }
           if (count < 32) break;
