@@ -297,10 +297,12 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
     }
     for (int c = tid; c < (C + 1) / 2; c += T) cnt32[c] = 0u;  // counters 0..C-1
     __syncthreads();
-    // ---- B: counting sort by cell
+    // ---- B: counting sort by cell (a bead's rank in its cell is kept in its
+    // force word, which is free until phase C and reset to zero here)
     for (int i = tid; i < N; i += T) {
       const int c = cellid[i];
-      atomicAdd(&cnt32[c >> 1], (c & 1) ? 65536u : 1u);
+      const unsigned old = atomicAdd(&cnt32[c >> 1], (c & 1) ? 65536u : 1u);
+      qfx[i] = (c & 1) ? static_cast<int>(old >> 16) : static_cast<int>(old & 0xffffu);
     }
     __syncthreads();
     {
@@ -335,13 +337,9 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
       if (tid == 0) cstart[C] = static_cast<unsigned short>(scan[NW - 1]);
     }
     __syncthreads();
-    for (int c = tid; c < (C + 1) / 2; c += T) cnt32[c] = 0u;  // counters 0..C-1
-    __syncthreads();
     for (int i = tid; i < N; i += T) {
-      const int c = cellid[i];
-      const unsigned old = atomicAdd(&cnt32[c >> 1], (c & 1) ? 65536u : 1u);
-      const int rank = (c & 1) ? static_cast<int>(old >> 16) : static_cast<int>(old & 0xffffu);
-      perm[cstart[c] + rank] = static_cast<unsigned short>(i);
+      perm[cstart[cellid[i]] + qfx[i]] = static_cast<unsigned short>(i);
+      qfx[i] = 0;  // fixed-point zero for C
     }
     __syncthreads();
     for (int c = tid; c < C; c += T) {  // ascending (x, id) inside each cell
@@ -409,23 +407,24 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
       atomicAdd(&qfx[j], -ix);
       atomicAdd(&qfy[j], -iy);
       atomicAdd(&qfz[j], -iz);
-      if (ikm) {
-        float wgt = 1.f;
-        if (ikm == 2) {
-          int cx, cy, cz;
-          cell_coords(cellid[i], nx, nxy, inx, inxy, cx, cy, cz);
-          const float rpx = static_cast<float>(cx) * wx + ox[i] - hx;
-          const float rpy = static_cast<float>(cy) * wy + oy[i] - hy;
-          const float rpz = static_cast<float>(cz) * wz + oz[i] - hz;
-          wgt = seg_fraction(rpx, rpy, rpz, rpx - rx, rpy - ry, rpz - rz, sB.half_core);
-        }
-        W[0] += wgt * Fx * rx;
-        W[1] += wgt * Fy * ry;
-        W[2] += wgt * Fz * rz;
-        W[3] += wgt * Fx * ry;
-        W[4] += wgt * Fx * rz;
-        W[5] += wgt * Fy * rz;
+      // IK bond weight: 0 outside the core's reach, 1 inside, else the
+      // segment fraction (only that case branches)
+      float wgt = ikm == 1 ? 1.f : 0.f;
+      if (ikm == 2) {
+        int cx, cy, cz;
+        cell_coords(cellid[i], nx, nxy, inx, inxy, cx, cy, cz);
+        const float rpx = static_cast<float>(cx) * wx + ox[i] - hx;
+        const float rpy = static_cast<float>(cy) * wy + oy[i] - hy;
+        const float rpz = static_cast<float>(cz) * wz + oz[i] - hz;
+        wgt = seg_fraction(rpx, rpy, rpz, rpx - rx, rpy - ry, rpz - rz, sB.half_core);
       }
+      const float wFx = wgt * Fx, wFy = wgt * Fy, wFz = wgt * Fz;
+      W[0] += wFx * rx;
+      W[1] += wFy * ry;
+      W[2] += wFz * rz;
+      W[3] += wFx * ry;
+      W[4] += wFx * rz;
+      W[5] += wFy * rz;
     };
 
     // Work items are (chunk of 32 consecutive sorted slots, row) pairs; each
@@ -603,7 +602,7 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
           __syncwarp();
           eval_pair(queue[lane]);
           __syncwarp();
-          if (lane < count - 32) queue[lane] = queue[32 + lane];
+          queue[lane] = queue[32 + lane];  // entries past count - 32 are dead
           __syncwarp();
           count -= 32;
         }
