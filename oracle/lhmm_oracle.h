@@ -53,6 +53,8 @@ typedef struct {
   int dpd_on_bonded;/* 1: DPD pair forces also act between bonded beads (sum over all j != i) */
   double alpha;       /* viscosity ratio (Eq. ratios) */
   double lambda_star; /* time-scale ratio (Eq. ratios) */
+  int dim;            /* 3, or 2: beads move in the x-y plane (z = 0, z edge unused,
+                         one cell layer, no z neighbours); volumes become areas */
 } orc_dpd_params;
 
 typedef struct {

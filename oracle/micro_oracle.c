@@ -28,6 +28,9 @@
  *     f_ij of Eq. potential_stress is the force on j due to i.
  *  R10 a bond at |r| >= R0 (Eq. fene_force undefined) is reported; its
  *     stiffness is held at the (r/R0)^2 = 0.99 value so the run continues.
+ *  R11 the paper's melt boxes are 2D (number density per area, Table 1):
+ *     dim = 2 keeps z = 0, one cell layer, pairs in the plane only, AFBC
+ *     squares, and the IK stress per core area.
  */
 #include "lhmm_oracle.h"
 
@@ -117,7 +120,7 @@ static void pair_disp(const orc_dpd_params* p, const orc_box* b, double gdot, in
 
 int orc_afbc_region(const orc_dpd_params* p, const double edge[3], const double r[3]) {
   int core = 1, bc = 1;
-  for (int a = 0; a < 3; ++a) {
+  for (int a = 0; a < (p->dim == 2 ? 2 : 3); ++a) {
     double x = fabs(r[a] - 0.5 * edge[a]);
     if (!(x < 0.5 * p->core_frac * edge[a])) core = 0;
     if (!(x < (0.5 * p->core_frac + p->bc_frac) * edge[a])) bc = 0;
@@ -144,9 +147,13 @@ double orc_segment_fraction(const double a[3], const double b[3], const double h
   return hi > lo ? hi - lo : 0.0;
 }
 
+/* volume (area in 2D) over which the IK stress averages (R9) */
 static double core_volume(const orc_dpd_params* p, const orc_box* b) {
-  if (p->flow_mode != ORC_FLOW_AFBC) return b->edge[0] * b->edge[1] * b->edge[2];
-  return p->core_frac * b->edge[0] * p->core_frac * b->edge[1] * p->core_frac * b->edge[2];
+  const int d = p->dim == 2 ? 2 : 3;
+  double v = 1.0;
+  for (int a = 0; a < d; ++a)
+    v *= (p->flow_mode == ORC_FLOW_AFBC ? p->core_frac : 1.0) * b->edge[a];
+  return v;
 }
 
 static int bonded(const orc_box* b, int i, int j) {
@@ -211,6 +218,7 @@ static double pair_ik_weight(const orc_dpd_params* p, const orc_box* b, int i, c
     c[k] = a[k] - dr[k];               /* image of j next to i */
     half[k] = 0.5 * p->core_frac * b->edge[k];
   }
+  if (p->dim == 2) half[2] = HUGE_VAL;  /* no z extent in 2D */
   return orc_segment_fraction(a, c, half);
 }
 
@@ -272,8 +280,10 @@ int orc_compute_forces(const orc_dpd_params* p, orc_box* b, const double L[9], i
   int nc[3];
   for (int a = 0; a < 3; ++a) {
     nc[a] = (int)floor(b->edge[a] / p->rc);
-    if (nc[a] < 3) return ORC_ERR_ARG;
+    if (a == 2 && p->dim == 2) nc[a] = 1; /* one layer, z = 0 */
+    else if (nc[a] < 3) return ORC_ERR_ARG;
   }
+  const int dz_max = p->dim == 2 ? 0 : 1;
   for (int k = 0; k < 3 * n; ++k) b->force[k] = 0.0;
 
   if (brute) {
@@ -306,7 +316,7 @@ int orc_compute_forces(const orc_dpd_params* p, orc_box* b, const double L[9], i
       double* Fi = &b->force[3 * i];
       int c = cellof[i];
       int cx = c % nc[0], cy = (c / nc[0]) % nc[1], cz = c / (nc[0] * nc[1]);
-      for (int dz = -1; dz <= 1; ++dz) {
+      for (int dz = -dz_max; dz <= dz_max; ++dz) {
         int z = (cz + dz + nc[2]) % nc[2];
         for (int dy = -1; dy <= 1; ++dy) {
           int yraw = cy + dy;

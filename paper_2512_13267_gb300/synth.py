@@ -27,6 +27,7 @@ DPD_PARAMS_PAPER_2D = dict(a_ij=25.0, gamma=4.5, sigma=3.0, kBT=1.0, rc=1.0, H_f
 AFBC_CORE_FRAC = 24.0 / 76.0   # Table 2: l_core / l_total
 AFBC_BC_FRAC = 13.0 / 76.0     # Table 2: l_bc / l_total
 DENSITY = 3.0
+DENSITY_PAPER_2D = 4.0  # Table 1: n_DPD (per area), dx = n^(-1/2) = 0.5
 CHAIN_LEN = 10
 POLYMER_FRACTION = 0.2
 
@@ -49,32 +50,48 @@ def serpentine_sites(n_side):
     return np.asarray(sites, dtype=np.int64)
 
 
+def serpentine_sites_2d(n_side):
+    """Square-lattice sites (ix, iy, 0) in boustrophedon order."""
+    sites = []
+    for iy in range(n_side):
+        xs = range(n_side) if iy % 2 == 0 else range(n_side - 1, -1, -1)
+        for ix in xs:
+            sites.append((ix, iy, 0))
+    return np.asarray(sites, dtype=np.int64)
+
+
 _SITE_CACHE = {}
 
 
 def initial_box_state(edge, n_beads, seed, box_id=0, kBT=1.0, mass=1.0, L=None,
-                      flow="afbc", jitter=0.1):
+                      flow="afbc", jitter=0.1, dim=3):
     """Initial positions (in [0, edge)) and velocities, float32, shape (n, 3).
 
     Beads sit on the first n_beads sites of a serpentine cubic lattice of
-    ceil(n^(1/3)) sites per side with uniform jitter of +-jitter spacing;
-    velocities are Maxwellian at kBT with the box mean removed, plus the
-    imposed streaming profile (u = L r' about the box centre for AFBC,
+    ceil(n^(1/3)) sites per side (square lattice of ceil(n^(1/2)) per side,
+    z = 0, for dim = 2) with uniform jitter of +-jitter spacing; velocities
+    are Maxwellian at kBT in each moving axis with the box mean removed, plus
+    the imposed streaming profile (u = L r' about the box centre for AFBC,
     u_x = L_xy (y - Ly/2) for Lees-Edwards)."""
     edge = np.broadcast_to(np.asarray(edge, dtype=np.float64), (3,))
     if n_beads == 0:
         return np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32)
     rng = np.random.default_rng([int(seed), int(box_id), 0x5EED])
-    n_side = int(np.ceil(n_beads ** (1.0 / 3.0) - 1e-9))
-    while n_side ** 3 < n_beads:
+    root = 2.0 if dim == 2 else 3.0
+    n_side = int(np.ceil(n_beads ** (1.0 / root) - 1e-9))
+    while n_side ** int(root) < n_beads:
         n_side += 1
-    if n_side not in _SITE_CACHE:
-        _SITE_CACHE[n_side] = serpentine_sites(n_side)
-    sites = _SITE_CACHE[n_side][:n_beads]
+    key = (n_side, dim)
+    if key not in _SITE_CACHE:
+        _SITE_CACHE[key] = serpentine_sites_2d(n_side) if dim == 2 else serpentine_sites(n_side)
+    sites = _SITE_CACHE[key][:n_beads]
     spacing = edge / n_side
     pos = (sites + 0.5) * spacing + rng.uniform(-jitter, jitter, size=(n_beads, 3)) * spacing
     pos = np.mod(pos, edge)
     vel = rng.normal(0.0, np.sqrt(kBT / mass), size=(n_beads, 3))
+    if dim == 2:
+        pos[:, 2] = 0.0
+        vel[:, 2] = 0.0
     vel -= vel.mean(axis=0, keepdims=True)
     if L is not None:
         L = np.asarray(L, dtype=np.float64).reshape(3, 3)
@@ -104,6 +121,7 @@ class BoxBatch:
     vel: np.ndarray = field(default=None)   # (N, 3) float32
     flow: str = "afbc"
     seed: int = 0
+    dim: int = 3
 
     @property
     def offsets(self):
@@ -123,10 +141,15 @@ class BoxBatch:
 
 
 def make_batch(edges, L, seed, flow="afbc", chain_len=CHAIN_LEN, fraction=POLYMER_FRACTION,
-               density=DENSITY, n_beads=None, kBT=1.0, with_state=True):
+               density=DENSITY, n_beads=None, kBT=1.0, with_state=True, dim=3):
+    """A batch of boxes with per-box gradients L (B x 9).  dim = 2: square
+    boxes in the x-y plane (z edge 1, unused), density per area."""
     edges = np.asarray(edges, dtype=np.float64)
     if edges.ndim == 1:
         edges = np.repeat(edges[:, None], 3, axis=1)
+    if dim == 2:
+        edges = edges.copy()
+        edges[:, 2] = 1.0
     B = edges.shape[0]
     if n_beads is None:
         n_beads = np.rint(density * np.prod(edges, axis=1)).astype(np.int32)
@@ -135,14 +158,14 @@ def make_batch(edges, L, seed, flow="afbc", chain_len=CHAIN_LEN, fraction=POLYME
                           dtype=np.int32)
     L = np.asarray(L, dtype=np.float32).reshape(B, 9)
     batch = BoxBatch(edges.astype(np.float32), n_beads, n_chains, chain_len, L, flow=flow,
-                     seed=seed)
+                     seed=seed, dim=dim)
     if with_state:
         pos = np.empty((batch.total_beads, 3), np.float32)
         vel = np.empty((batch.total_beads, 3), np.float32)
         for b in range(B):
             sl = batch.box_slice(b)
             p, v = initial_box_state(edges[b], int(n_beads[b]), seed, b, kBT=kBT, L=L[b],
-                                     flow=flow)
+                                     flow=flow, dim=dim)
             pos[sl] = p
             vel[sl] = v
         batch.pos, batch.vel = pos, vel
@@ -257,3 +280,19 @@ def coupled_channel(nx=64, ny=32, Ly=4.0, box_beads=1500, seed=3, c_factor=10.0,
                mass=dh * dh, rho0=1.0, c=c, eta_s=eta_s, body_force=F, substeps=M,
                dt=delta_t / M)
     return sph, batch
+
+
+def melt_rheometer_batch(chain_len, shear_rates, replicas, edge=20.0, seed=11,
+                         density=DENSITY_PAPER_2D):
+    """2D polymer melts of the paper's micro model (Table 1: number density 4,
+    all beads in chains of chain_len) in square periodic boxes under
+    Lees-Edwards shear: `replicas` boxes per shear rate, box b sheared at
+    shear_rates[b // replicas] (L_xy)."""
+    rates = np.repeat(np.asarray(shear_rates, dtype=np.float64), int(replicas))
+    B = rates.shape[0]
+    L = np.zeros((B, 9), np.float32)
+    L[:, 1] = rates
+    n = int(round(density * edge * edge))
+    n -= n % chain_len
+    return make_batch(np.full(B, edge), L, seed, flow="lees_edwards", chain_len=chain_len,
+                      fraction=1.0, n_beads=np.full(B, n), dim=2)
