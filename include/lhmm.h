@@ -78,6 +78,11 @@ typedef struct {
   int dpd_on_bonded;    /* 1: DPD pair forces also act on bonded pairs (sum over all j != i) */
   double alpha;         /* viscosity ratio alpha, Eq. ratios; output is scaled by alpha/lambda* */
   double lambda_star;   /* time-scale ratio lambda*, Eq. ratios; input L is scaled by lambda* */
+  int dim;              /* 3, or 2 for the paper's planar melt boxes (Table 1): beads move in
+                           the x-y plane (z components of positions, velocities and forces are
+                           set to 0, the z edge is ignored), one cell layer, pairs in the plane,
+                           AFBC squares, IK stress per core area.  0 means 3; other values
+                           return LHMM_ERR_ARG. */
 } lhmm_dpd_params;
 
 /* A batch of independent boxes.  Box b has edges box_edge[3b..3b+2] (its

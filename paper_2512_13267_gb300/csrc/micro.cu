@@ -74,6 +74,7 @@ struct MicroArgs {
   double out_scale;
   unsigned seed_lo, seed_hi;
   int flow, dpd_on_bonded, chain_len;
+  int n_rows;                // rows of the upper half-stencil: 5 in 3D, 2 in 2D
   int max_beads, max_cells;
   int n_boxes;
   int* work_counter;         // persistent mode: next work item (NULL: one block per item)
@@ -431,14 +432,15 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
     // warp takes a contiguous share of them, so the block stays balanced when
     // the bead count is not a multiple of the block size.
     int count = 0;  // warp-uniform queue fill
-    const int n_items = 5 * ((N + 31) >> 5);
+    const int n_rows = A.n_rows;
+    const int n_items = n_rows * ((N + 31) >> 5);
     const int per_warp = (n_items + NW - 1) / NW;
     const int it_end = min(n_items, (warp + 1) * per_warp);
     int cur_chunk = -1;
     int k = 0, i = 0, cx = 0, cy = 0, cz = 0, ikm = 1;
     float xi = 0.f, yi = 0.f, zi = 0.f;
     for (int it = warp * per_warp; it < it_end; ++it) {
-      const int chunk = it / 5, row = it - 5 * chunk;
+      const int chunk = it / n_rows, row = it - n_rows * chunk;
       if (chunk != cur_chunk) {  // warp-uniform: load bead k = 32 chunk + lane
         cur_chunk = chunk;
         k = (chunk << 5) + lane;
@@ -954,6 +956,7 @@ MicroArgs make_args(const lhmm_micro_s* h) {
   a.seed_hi = static_cast<unsigned>(p.seed >> 32);
   a.flow = p.flow_mode;
   a.dpd_on_bonded = p.dpd_on_bonded;
+  a.n_rows = p.dim == 2 ? 2 : 5;
   a.chain_len = h->chain_len > 0 ? h->chain_len : 1;
   a.max_beads = h->max_beads;
   a.max_cells = h->max_cells;
@@ -998,8 +1001,10 @@ extern "C" lhmm_status lhmm_micro_create(const lhmm_dpd_params* params,
   *out = nullptr;
   const lhmm_dpd_params& p = *params;
   if (!(p.rc > 0.f) || !(p.dt > 0.f) || !(p.mass > 0.f) || !(p.R0 > 0.f) ||
-      !(p.lambda_star != 0.0) || p.flow_mode < 0 || p.flow_mode > 2)
+      !(p.lambda_star != 0.0) || p.flow_mode < 0 || p.flow_mode > 2 ||
+      (p.dim != 0 && p.dim != 2 && p.dim != 3))
     return LHMM_ERR_ARG;
+  const bool planar = p.dim == 2;
   const int nb = batch->n_boxes;
   if (nb > 0 && (!batch->box_edge || !batch->n_beads || !batch->n_chains)) return LHMM_ERR_ARG;
   std::vector<BoxInfo> info(nb);
@@ -1017,6 +1022,12 @@ extern "C" lhmm_status lhmm_micro_create(const lhmm_dpd_params* params,
     long long ncell = 1;
     float vol = 1.f;
     for (int a = 0; a < 3; ++a) {
+      if (a == 2 && planar) {  // one layer of unit depth that nothing leaves
+        B.nc[2] = 1;
+        B.w[2] = B.winv[2] = B.len[2] = 1.f;
+        B.half_core[2] = B.half_bc[2] = 1e30f;
+        continue;
+      }
       const float E = batch->box_edge[3 * b + a];
       if (!(E >= 3.f * p.rc)) return LHMM_ERR_ARG;
       B.nc[a] = static_cast<int>(std::floor(E / p.rc));
@@ -1121,7 +1132,8 @@ extern "C" lhmm_status lhmm_micro_create(const lhmm_dpd_params* params,
     abs_to_rel(B, pos0_host + 3 * B.off, pos.data() + B.off, B.n);
     for (int i = 0; i < B.n; ++i) {
       const float* v = vel0_host + 3 * (B.off + i);
-      vel[B.off + i] = make_float4(v[0], v[1], v[2], 0.f);
+      vel[B.off + i] = make_float4(v[0], v[1], planar ? 0.f : v[2], 0.f);
+      if (planar) pos[B.off + i].z = 0.f;
     }
   }
   std::vector<BoxState> st(nbx);
@@ -1288,13 +1300,16 @@ extern "C" lhmm_status lhmm_micro_set_state(lhmm_micro_t h, int box, const doubl
   const BoxInfo& B = h->info[box];
   if (B.n) {
     std::vector<float4> buf(static_cast<size_t>(B.n));
+    const bool planar = h->p.dim == 2;  // z components are zero in 2D
     abs_to_rel(B, pos_host, buf.data(), B.n);
+    if (planar)
+      for (int i = 0; i < B.n; ++i) buf[i].z = 0.f;
     LHMM_CK(cudaMemcpy(h->pos_d + B.off, buf.data(), sizeof(float4) * B.n, cudaMemcpyHostToDevice));
     for (int i = 0; i < B.n; ++i)
-      buf[i] = make_float4(vel_host[3 * i], vel_host[3 * i + 1], vel_host[3 * i + 2], 0.f);
+      buf[i] = make_float4(vel_host[3 * i], vel_host[3 * i + 1], planar ? 0.f : vel_host[3 * i + 2], 0.f);
     LHMM_CK(cudaMemcpy(h->vel_d + B.off, buf.data(), sizeof(float4) * B.n, cudaMemcpyHostToDevice));
     for (int i = 0; i < B.n; ++i)
-      buf[i] = make_float4(force_host[3 * i], force_host[3 * i + 1], force_host[3 * i + 2], 0.f);
+      buf[i] = make_float4(force_host[3 * i], force_host[3 * i + 1], planar ? 0.f : force_host[3 * i + 2], 0.f);
     LHMM_CK(cudaMemcpy(h->frc_d + B.off, buf.data(), sizeof(float4) * B.n, cudaMemcpyHostToDevice));
   }
   BoxState s{step, le_offset, 0u};

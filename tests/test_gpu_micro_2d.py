@@ -1,0 +1,124 @@
+"""GPU parity of the planar (dim = 2) micro engine against the FP64 oracle:
+the paper's melt boxes (Table 1 parameters, number density 4 per area, all
+beads in chains).  Same tolerances as the 3D tests: single-step forces
+max |dF| <= 1e-4, 50-step positions <= 1e-3, time-averaged stresses within
+3 combined block standard errors."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2512_13267_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+PAPER = dict(a_ij=25.0, gamma=4.5, sigma=3.0, H_fene=50.0, R0=1.5, dt=0.005)
+FLOW_O = {"periodic": O.FLOW_PERIODIC, "lees_edwards": O.FLOW_LEES_EDWARDS, "afbc": O.FLOW_AFBC}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def _batch(flow, seed, nd=8):
+    edges = np.array([3.0, 5.0, 8.0, 12.0, 20.0])
+    B = len(edges)
+    if flow == "lees_edwards":
+        L = np.zeros((B, 9), np.float32)
+        L[:, 1] = np.array([0.05, 0.1, 0.2, 0.3, 0.5])
+    elif flow == "afbc":
+        L = S.random_velocity_gradients(B, seed, rate_range=(0.05, 0.5))
+        L = L.reshape(B, 3, 3)
+        L[:, 2, :] = 0.0
+        L[:, :, 2] = 0.0  # the planar flow of an SPH particle
+        L = L.reshape(B, 9)
+    else:
+        L = np.zeros((B, 9), np.float32)
+    n = np.rint(4 * edges * edges).astype(int)
+    n -= n % nd
+    return S.make_batch(edges, L, seed, flow=flow, chain_len=nd, fraction=1.0, n_beads=n, dim=2)
+
+
+def _pair(batch, flow, seed):
+    from paper_2512_13267_gb300 import lhmm as lh
+    gp = lh.dpd_params(flow=flow, seed=seed, dim=2, **PAPER)
+    op = O.dpd_params(flow_mode=FLOW_O[flow], seed=seed, dim=2, **PAPER)
+    m = lh.Micro.from_batch(gp, batch)
+    boxes = []
+    for b in range(batch.n_boxes):
+        sl = batch.box_slice(b)
+        ob = O.Box(batch.edges[b], batch.pos[sl], batch.vel[sl], int(batch.n_chains[b]),
+                   batch.chain_len, box_id=b)
+        O.compute_forces(op, ob, batch.L[b])
+        boxes.append(ob)
+    return m, op, boxes
+
+
+def _minimage(d, E):
+    return d - E * np.rint(d / E)
+
+
+@pytest.mark.parametrize("flow", ["periodic", "lees_edwards", "afbc"])
+def test_2d_initial_forces_match_oracle(flow):
+    batch = _batch(flow, 3)
+    m, op, boxes = _pair(batch, flow, 3)
+    for b, ob in enumerate(boxes):
+        pos, vel, f, step, _ = m.get_state(b)
+        assert np.all(f[:, 2] == 0.0) and np.all(pos[:, 2] == 0.0)
+        assert np.abs(f - ob.force).max() <= 1e-4, (b, np.abs(f - ob.force).max())
+    m.close()
+
+
+@pytest.mark.parametrize("flow", ["periodic", "lees_edwards", "afbc"])
+def test_2d_fifty_step_trajectory(flow):
+    batch = _batch(flow, 8)
+    m, op, boxes = _pair(batch, flow, 9)
+    L = torch.from_numpy(batch.L).cuda()
+    st = torch.zeros((batch.n_boxes, 6), dtype=torch.float64, device="cuda")
+    m.advance(L, 50, st)
+    m.sync()
+    got = st.cpu().numpy()
+    for b, ob in enumerate(boxes):
+        ref, _, err = O.advance(op, ob, batch.L[b], 50)
+        assert err == 0
+        pos, vel, f, step, _ = m.get_state(b)
+        assert step == 50 and np.all(pos[:, 2] == 0.0) and np.all(vel[:, 2] == 0.0)
+        dpos = np.abs(_minimage(pos - ob.pos, batch.edges[b][0])).max()
+        assert dpos <= 1e-3, (b, dpos)
+        scale = 1.0 + np.abs(ref).max()
+        assert np.abs(got[b] - ref).max() <= 2e-2 * scale, (b, got[b], ref)
+        assert got[b][2] == 0.0 and got[b][4] == 0.0 and got[b][5] == 0.0
+    m.close()
+
+
+def test_2d_block_averaged_shear_stress_of_a_melt():
+    # a 12 x 12 melt of N_d = 4 chains under shear 0.05, 30 calls of 200
+    # steps: GPU and oracle block means within 3 combined SEs
+    batch = S.melt_rheometer_batch(4, [0.05], 1, edge=12.0, seed=4)
+    m, op, boxes = _pair(batch, "lees_edwards", 4)
+    L = torch.from_numpy(batch.L).cuda()
+    st = torch.zeros((1, 6), dtype=torch.float64, device="cuda")
+    g_blocks, o_blocks = [], []
+    for _ in range(30):
+        m.advance(L, 200, st)
+        g_blocks.append(st.cpu().numpy()[0].copy())
+        ref, _, _ = O.advance(op, boxes[0], batch.L[0], 200)
+        o_blocks.append(ref)
+    m.sync()
+    g = np.asarray(g_blocks)[5:]
+    o = np.asarray(o_blocks)[5:]
+    se = np.sqrt(g.var(axis=0, ddof=1) / len(g) + o.var(axis=0, ddof=1) / len(o))
+    diff = np.abs(g.mean(axis=0) - o.mean(axis=0))
+    assert np.all(diff <= 3 * se + 1e-6), (g.mean(0), o.mean(0), se)
+    assert g.mean(axis=0)[3] > 0
+    m.close()
+
+
+def test_2d_rejects_bad_dim():
+    from paper_2512_13267_gb300 import lhmm as lh
+    batch = _batch("periodic", 1)
+    with pytest.raises(lh.LhmmError):
+        lh.Micro.from_batch(lh.dpd_params(flow="periodic", dim=4, **PAPER), batch)
