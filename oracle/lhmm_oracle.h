@@ -55,6 +55,8 @@ typedef struct {
   double lambda_star; /* time-scale ratio (Eq. ratios) */
   int dim;            /* 3, or 2: beads move in the x-y plane (z = 0, z edge unused,
                          one cell layer, no z neighbours); volumes become areas */
+  int exclude_bonds;  /* K in 0..3: no DPD pair force between beads of one chain at
+                         most K bonds apart (dpd_on_bonded = 0 means at least 1) */
 } orc_dpd_params;
 
 typedef struct {

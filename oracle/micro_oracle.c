@@ -15,7 +15,9 @@
  *     the first two output words, so theta_ij = theta_ji.
  *  R4 FENE: attractive, F_i = -H r_ij / (1 - (r/R0)^2); Eq. fene_force drops
  *     the minus sign that its commented -grad U states.
- *  R5 the DPD sum of Eq. F_DPD runs over all j != i, bonded pairs included.
+ *  R5 the DPD sum of Eq. F_DPD runs over all j != i, bonded pairs included
+ *     (alternatives: exclude pairs of one chain up to K bonds apart, as a
+ *     LAMMPS special_bonds setting does).
  *  R6 velocity-Verlet in the LAMMPS form named by the coupling protocol:
  *     half kick, drift, forces (dissipative term with half-step v), half kick.
  *  R7 Lees-Edwards sliding-brick images for steady shear du_x/dy.
@@ -156,11 +158,15 @@ static double core_volume(const orc_dpd_params* p, const orc_box* b) {
   return v;
 }
 
-static int bonded(const orc_box* b, int i, int j) {
-  int lo = i < j ? i : j, hi = i < j ? j : i;
-  if (hi != lo + 1) return 0;
+/* pair (i, j) excluded from the DPD sum: same chain, at most K bonds apart,
+ * K = max(exclude_bonds, 1 if dpd_on_bonded = 0) (R5 and its alternatives) */
+static int excluded(const orc_dpd_params* p, const orc_box* b, int i, int j) {
+  int K = p->exclude_bonds > 0 ? p->exclude_bonds : 0;
+  if (!p->dpd_on_bonded && K < 1) K = 1;
+  int lo = i < j ? i : j, hi = i < j ? j : i, d = hi - lo;
+  if (d < 1 || d > K) return 0;
   if (hi >= b->n_chains * b->chain_len) return 0;
-  return (hi % b->chain_len) != 0; /* same chain */
+  return (lo % b->chain_len) + d < b->chain_len; /* same chain */
 }
 
 /* ------------------------------------------------------------------ */
@@ -239,8 +245,7 @@ static int accumulate_pair(const orc_dpd_params* p, orc_box* b, double gdot, int
   double dr[3], dv[3], F[3];
   int hit, err = 0;
   pair_disp(p, b, gdot, i, j, dr, dv);
-  int bond = bonded(b, i, j);
-  if (!bond || p->dpd_on_bonded) {
+  if (!excluded(p, b, i, j)) {
     dpd_pair_force(p, b, i, j, dr, dv, F, &hit);
     if (hit) {
       Fi[0] += F[0]; Fi[1] += F[1]; Fi[2] += F[2];

@@ -247,3 +247,34 @@ def test_lees_edwards_linear_streaming_profile():
     # and the shear stress the IK formula returns is positive (eta_p > 0)
     mean, _, _ = O.advance(par, b, L, 400)
     assert mean[3] > 0
+
+
+@pytest.mark.parametrize("K,expected", [(0, 30.0), (1, 12.5), (2, 2.5), (3, 0.0)])
+def test_bond_exclusion_depth(K, expected):
+    # beads 0..3 form one chain on a line at spacing 0.3 (all within rc):
+    # the conservative force on bead 0 sums a (1 - r) over the pairs that the
+    # exclusion depth K keeps (r = 0.3, 0.6, 0.9 for 1, 2, 3 bonds apart)
+    par = O.dpd_params(flow_mode=O.FLOW_PERIODIC, gamma=0.0, sigma=0.0, H_fene=0.0,
+                       exclude_bonds=K)
+    x = np.array([[1.0 + 0.3 * k, 2.0, 2.0] for k in range(4)])
+    b = O.Box(5.0, x, np.zeros((4, 3)), n_chains=1, chain_len=4)
+    f, _, err = O.compute_forces(par, b)
+    assert err == 0
+    assert abs(f[0, 0] + expected) < 1e-12 and abs(f[0, 1]) < 1e-12
+    assert np.abs(f.sum(axis=0)).max() < 1e-12
+
+
+def test_bond_exclusion_stops_at_chain_ends():
+    # two 2-bead chains: ids 1 and 2 are consecutive but in different chains,
+    # so even K = 3 keeps their pair force; dpd_on_bonded = 0 means K >= 1
+    par = O.dpd_params(flow_mode=O.FLOW_PERIODIC, gamma=0.0, sigma=0.0, H_fene=0.0,
+                       dpd_on_bonded=0)
+    x = np.array([[1.0, 2.0, 2.0], [1.3, 2.0, 2.0], [1.6, 2.0, 2.0], [1.9, 2.0, 2.0]])
+    b = O.Box(5.0, x, np.zeros((4, 3)), n_chains=2, chain_len=2)
+    f, _, _ = O.compute_forces(par, b)
+    # bead 1: pairs (1,0) excluded, (1,2) r = 0.3 kept, (1,3) r = 0.6 kept
+    assert abs(f[1, 0] - (-25.0 * 0.7 - 25.0 * 0.4)) < 1e-12
+    par3 = O.dpd_params(flow_mode=O.FLOW_PERIODIC, gamma=0.0, sigma=0.0, H_fene=0.0,
+                        exclude_bonds=3)
+    f3, _, _ = O.compute_forces(par3, b)
+    assert np.array_equal(f3, f)
