@@ -83,6 +83,10 @@ typedef struct {
                            set to 0, the z edge is ignored), one cell layer, pairs in the plane,
                            AFBC squares, IK stress per core area.  0 means 3; other values
                            return LHMM_ERR_ARG. */
+  int exclude_bonds;    /* K in 0..3: no DPD pair force (C, D, R) between beads of one chain
+                           at most K bonds apart (LAMMPS special_bonds lj 0 0 0 is K = 3);
+                           dpd_on_bonded = 0 means K >= 1.  FENE bonds are unaffected.
+                           Other values return LHMM_ERR_ARG. */
 } lhmm_dpd_params;
 
 /* A batch of independent boxes.  Box b has edges box_edge[3b..3b+2] (its

@@ -75,6 +75,7 @@ struct MicroArgs {
   unsigned seed_lo, seed_hi;
   int flow, dpd_on_bonded, chain_len;
   int n_rows;                // rows of the upper half-stencil: 5 in 3D, 2 in 2D
+  int excl;                  // DPD pairs of one chain up to excl bonds apart are skipped
   int max_beads, max_cells;
   int n_boxes;
   int* work_counter;         // persistent mode: next work item (NULL: one block per item)
@@ -586,9 +587,9 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
               const float rz = zb - oz[j];
               const float r2 = rx * rx + ry * ry + rz * rz;
               hit = act && (r2 < A.rc2) && (r2 > 0.f);
-              if (!A.dpd_on_bonded) {  // uniform: bonded pairs skip DPD (reading R5 off)
-                const int lo = min(i, j), hi = max(i, j);
-                hit = hit && !(hi == lo + 1 && hi < sB.n_poly && (hi % A.chain_len) != 0);
+              if (A.excl > 0) {  // uniform: pairs of one chain <= excl bonds apart skip DPD
+                const int lo = min(i, j), d = max(i, j) - lo;
+                hit = hit && !(d <= A.excl && lo + d < sB.n_poly && (lo % A.chain_len) + d < A.chain_len);
               }
               lo_w = lo_i | (static_cast<unsigned>(j) << 16);
               hi_w = (first ? hw1 : hw2) + static_cast<unsigned>(p0) + static_cast<unsigned>(p1);
@@ -957,6 +958,7 @@ MicroArgs make_args(const lhmm_micro_s* h) {
   a.flow = p.flow_mode;
   a.dpd_on_bonded = p.dpd_on_bonded;
   a.n_rows = p.dim == 2 ? 2 : 5;
+  a.excl = std::max(p.exclude_bonds, p.dpd_on_bonded ? 0 : 1);
   a.chain_len = h->chain_len > 0 ? h->chain_len : 1;
   a.max_beads = h->max_beads;
   a.max_cells = h->max_cells;
@@ -1002,7 +1004,7 @@ extern "C" lhmm_status lhmm_micro_create(const lhmm_dpd_params* params,
   const lhmm_dpd_params& p = *params;
   if (!(p.rc > 0.f) || !(p.dt > 0.f) || !(p.mass > 0.f) || !(p.R0 > 0.f) ||
       !(p.lambda_star != 0.0) || p.flow_mode < 0 || p.flow_mode > 2 ||
-      (p.dim != 0 && p.dim != 2 && p.dim != 3))
+      (p.dim != 0 && p.dim != 2 && p.dim != 3) || p.exclude_bonds < 0 || p.exclude_bonds > 3)
     return LHMM_ERR_ARG;
   const bool planar = p.dim == 2;
   const int nb = batch->n_boxes;

@@ -28,14 +28,17 @@ def carreau_yasuda(gdot, eta0, eta_inf, lam, a, n):
 
 
 def melt_viscosity(chain_len, shear_rates, replicas=32, edge=20.0, equil_time=None,
-                   sample_time=None, call_steps=1000, seed=11):
+                   sample_time=None, call_steps=1000, seed=11, dpd_on_bonded=1,
+                   exclude_bonds=0):
     """Steady-shear viscosity and psi_1 of a 2D melt of chain_len-bead chains.
 
     Returns per shear rate the replica mean and standard error of eta and
     psi_1, plus run counts.  equil_time / sample_time (DPD time units)
     default to 5 and 10 Rouse-scaled relaxation times of the chain
     (23.5 (chain_len / 4)^2, the N_d = 4 value of Table 3 with Rouse scaling),
-    at least 100 and 200."""
+    at least 100 and 200.  dpd_on_bonded = 0 drops the DPD pair forces
+    between bonded neighbours, exclude_bonds = K those of beads of one chain
+    up to K bonds apart (reading R5's alternatives)."""
     import torch
     rates = np.asarray(shear_rates, dtype=np.float64)
     lam_guess = 23.5 * (chain_len / 4.0) ** 2
@@ -45,7 +48,8 @@ def melt_viscosity(chain_len, shear_rates, replicas=32, edge=20.0, equil_time=No
     n_equil = int(np.ceil(equil_time / dt / call_steps))
     n_sample = int(np.ceil(sample_time / dt / call_steps))
     batch = synth.melt_rheometer_batch(chain_len, rates, replicas, edge=edge, seed=seed)
-    params = lhmm.dpd_params(flow="lees_edwards", seed=seed, dim=2, **PAPER_2D)
+    params = lhmm.dpd_params(flow="lees_edwards", seed=seed, dim=2, dpd_on_bonded=dpd_on_bonded,
+                             exclude_bonds=exclude_bonds, **PAPER_2D)
     t0 = time.perf_counter()
     m = lhmm.Micro.from_batch(params, batch)
     L = torch.from_numpy(batch.L).cuda()
@@ -66,6 +70,7 @@ def melt_viscosity(chain_len, shear_rates, replicas=32, edge=20.0, equil_time=No
     se = lambda x: x.std(axis=1, ddof=1) / np.sqrt(x.shape[1])
     m.close()
     return dict(chain_len=chain_len, shear_rates=rates.tolist(), replicas=replicas, edge=edge,
+                dpd_on_bonded=dpd_on_bonded, exclude_bonds=exclude_bonds,
                 beads_per_box=int(batch.n_beads[0]), boxes=batch.n_boxes,
                 eta=eta.mean(axis=1).tolist(), eta_se=se(eta).tolist(),
                 psi1=psi1.mean(axis=1).tolist(), psi1_se=se(psi1).tolist(),

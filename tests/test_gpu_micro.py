@@ -331,3 +331,13 @@ def test_autotune_keeps_state_and_plan_is_valid():
     assert np.allclose(s1.cpu().numpy(), s2.cpu().numpy(), rtol=1e-3, atol=1e-3)
     m.close()
     m2.close()
+
+
+def test_bonded_pairs_excluded_matches_oracle():
+    # dpd_on_bonded = 0: no DPD pair force between chain neighbours
+    batch = _ragged_afbc_batch(seed=6)
+    m, op, boxes = _pair(batch, "afbc", seed=6, dpd_on_bonded=0)
+    for b, ob in enumerate(boxes):
+        _, _, f, _, _ = m.get_state(b)
+        assert np.abs(f - ob.force).max() <= 1e-4, (b, np.abs(f - ob.force).max())
+    m.close()

@@ -122,3 +122,31 @@ def test_2d_rejects_bad_dim():
     batch = _batch("periodic", 1)
     with pytest.raises(lh.LhmmError):
         lh.Micro.from_batch(lh.dpd_params(flow="periodic", dim=4, **PAPER), batch)
+
+
+@pytest.mark.parametrize("K", [1, 3])
+def test_2d_bond_exclusion_matches_oracle(K):
+    # DPD pairs of one chain up to K bonds apart skipped on both sides
+    from paper_2512_13267_gb300 import lhmm as lh
+    batch = _batch("lees_edwards", 12, nd=4)
+    gp = lh.dpd_params(flow="lees_edwards", seed=5, dim=2, exclude_bonds=K, **PAPER)
+    op = O.dpd_params(flow_mode=O.FLOW_LEES_EDWARDS, seed=5, dim=2, exclude_bonds=K, **PAPER)
+    m = lh.Micro.from_batch(gp, batch)
+    L = torch.from_numpy(batch.L).cuda()
+    st = torch.zeros((batch.n_boxes, 6), dtype=torch.float64, device="cuda")
+    boxes = []
+    for b in range(batch.n_boxes):
+        sl = batch.box_slice(b)
+        ob = O.Box(batch.edges[b], batch.pos[sl], batch.vel[sl], int(batch.n_chains[b]),
+                   batch.chain_len, box_id=b)
+        O.compute_forces(op, ob, batch.L[b])
+        _, _, f, _, _ = m.get_state(b)
+        assert np.abs(f - ob.force).max() <= 1e-4, (b, np.abs(f - ob.force).max())
+        boxes.append(ob)
+    m.advance(L, 50, st)
+    m.sync()
+    for b, ob in enumerate(boxes):
+        O.advance(op, ob, batch.L[b], 50)
+        pos, _, _, _, _ = m.get_state(b)
+        assert np.abs(_minimage(pos - ob.pos, batch.edges[b][0])).max() <= 1e-3
+    m.close()
