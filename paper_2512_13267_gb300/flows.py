@@ -1,0 +1,107 @@
+"""Coupled LHMM runs of the paper's reverse-Poiseuille benchmark (Sec. 6.1).
+
+Reverse-Poiseuille flow (RPF): a periodic square of side L_y, body force +F
+(per unit mass) in the upper half and -F in the lower half.  Momentum
+balance fixes the steady total shear stress exactly, whatever the polymer
+closure:
+    tau_xy(y) = F rho (L_y/4 - y)       for y <  L_y/2,
+    tau_xy(y) = F rho (y - 3 L_y/4)     for y >= L_y/2     (Eq. RPF),
+where tau is the momentum flux, minus the Cauchy shear stress sigma_xy that
+the momentum equation dv/dt = div(sigma)/rho + f uses (reading R14: steady
+d sigma_xy/dy = -rho f_x with zero mean gives sigma_xy = F rho (y - L_y/4) in
+the lower half).  The time-averaged solvent + polymer sigma_xy of a
+converged coupled run is checked against -tau_xy.  The set-up follows
+the paper: L_x = L_y = 4, dh = 0.1 (40 x 40 particles), Lucy kernel with
+h = 4 dh, rho = 1, eta_s = 0.02, Delta t_SPH = 0.04, coupling interval
+delta t = 0.32 = 64 DPD steps of 0.005, one 2D melt box per particle
+(Table 1 parameters, AFBC squares).  The paper's boxes are 76 x 76; here
+they are box_edge x box_edge (the engine keeps a box in one SM's shared
+memory).
+"""
+import time
+
+import numpy as np
+
+from . import lhmm, rheometry, synth
+
+
+def rpf_exact_shear_stress(y, F, Ly, rho=1.0):
+    """Eq. RPF: the steady total shear stress of reverse-Poiseuille flow."""
+    y = np.asarray(y, dtype=np.float64)
+    return np.where(y < 0.5 * Ly, F * rho * (0.25 * Ly - y), F * rho * (y - 0.75 * Ly))
+
+
+def rpf_paper(F=1e-3, chain_len=8, alpha=1e-4, n_macro=1000, n_avg=300, box_edge=20.0,
+              nbins=20, seed=3, c=0.25, eta_s=0.02, exclude_bonds=0, timing_steps=50,
+              dh=0.1, dt_sph=0.04):
+    """Run the coupled RPF of Sec. 6.1 and compare the time-averaged binned
+    total shear stress sigma_xy = eta_s (L_xy + L_yx) + pi_xy (pi as the SPH
+    momentum equation uses it) with -tau_xy of Eq. RPF over the last n_avg of
+    n_macro macro steps.  Returns the profiles, the relative L2 error, the
+    largest error over tau_max = F rho L_y / 4, and macro-steps/s."""
+    import torch
+    Ly = Lx = 4.0
+    n_side = int(round(Ly / dh))
+    pos = synth.sph_lattice(n_side, n_side, Lx, Ly)
+    n = pos.shape[0]
+    k_micro = 64
+    M = int(round(k_micro * rheometry.PAPER_2D["dt"] / dt_sph))  # 0.32 / 0.04 = 8
+    sp = lhmm.sph_params(n, 0, Lx=Lx, Ly=Ly, h=4.0 * dh, mass=dh * dh, rho0=1.0, c=c,
+                         theta_pb=0.1, eta_s=eta_s, dt=dt_sph, kernel=lhmm.SPH_LUCY,
+                         body_force=(F, 0.0), body_mode=lhmm.SPH_BODY_REVERSE_POISEUILLE)
+    sph = lhmm.Sph(sp, pos, np.zeros_like(pos))
+    nb = int(round(4 * box_edge * box_edge))
+    nb -= nb % chain_len
+    batch = synth.make_batch(np.full(n, box_edge), np.zeros((n, 9), np.float32), seed,
+                             flow="afbc", chain_len=chain_len, fraction=1.0,
+                             n_beads=np.full(n, nb), dim=2)
+    micro = lhmm.Micro.from_batch(
+        lhmm.dpd_params(flow="afbc", seed=seed, dim=2, alpha=alpha, exclude_bonds=exclude_bonds,
+                        **rheometry.PAPER_2D), batch)
+    L0 = torch.zeros((n, 9), dtype=torch.float32, device="cuda")
+    micro.autotune(L0, probe_steps=8)
+    cpl = lhmm.Coupled(sph, micro, M, k_micro)
+    t0 = time.perf_counter()
+    cpl.step(n_macro - n_avg, use_graph=True)
+    edges = np.linspace(0.0, Ly, nbins + 1)
+    acc = np.zeros(nbins)
+    acc_p = np.zeros(nbins)
+    cnt = np.zeros(nbins)
+    for _ in range(n_avg):
+        cpl.step(1, use_graph=True)
+        y = sph.get_state()[0][:, 1]
+        Lg, st = cpl.exchange()
+        tau = eta_s * (Lg[:, 1] + Lg[:, 3]) + st[:, 3]
+        k = np.clip(np.searchsorted(edges, y, side="right") - 1, 0, nbins - 1)
+        acc += np.bincount(k, weights=tau, minlength=nbins)
+        acc_p += np.bincount(k, weights=st[:, 3], minlength=nbins)
+        cnt += np.bincount(k, minlength=nbins)
+    wall = time.perf_counter() - t0
+    prof = acc / np.maximum(cnt, 1)
+    prof_p = acc_p / np.maximum(cnt, 1)
+    yc = 0.5 * (edges[1:] + edges[:-1])
+    exact = -rpf_exact_shear_stress(yc, F, Ly)  # sigma_xy = -tau_xy
+    tau_max = F * Ly / 4.0
+    # timing of graph-replayed macro steps alone
+    s = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    cpl.step(timing_steps, use_graph=True)
+    e1.record(s)
+    e1.synchronize()
+    rate = timing_steps / (e0.elapsed_time(e1) / 1e3)
+    status = lhmm.status_string(micro.sync(raise_on_error=False)[0])
+    out = dict(F=F, chain_len=chain_len, alpha=alpha, particles=n, box_beads=nb,
+               beads=int(batch.total_beads), sph_substeps=M, micro_steps=k_micro,
+               n_macro=n_macro, n_avg=n_avg, y=yc.tolist(), sigma_total=prof.tolist(),
+               sigma_exact=exact.tolist(), sigma_polymer=prof_p.tolist(),
+               rel_l2_error=float(np.linalg.norm(prof - exact) / np.linalg.norm(exact)),
+               max_abs_error_over_tau_max=float(np.abs(prof - exact).max() / tau_max),
+               polymer_share=float(np.abs(prof_p).sum() / max(np.abs(prof).sum(), 1e-30)),
+               macro_steps_per_s=rate,
+               bead_steps_per_s=rate * batch.total_beads * k_micro, wall_s=wall,
+               device_status=status)
+    for o in (cpl, micro, sph):
+        o.close()
+    return out
