@@ -29,8 +29,9 @@ sys.path.insert(0, ROOT)
 METRIC = "DPD bead-steps/s (batched micro boxes)"
 UNIT = "bead-steps/s"
 MICRO_STEPS = 100
-# Algorithmic lane-operations per bead-step (each unique interacting pair
-# once, no rejected candidates); derivation in the design doc.
+# Algorithmic lane-operations per bead-step: each unique interacting pair
+# once, no rejected candidates (the per-pair and per-bead counts below list
+# their parts).
 PAIRS_PER_BEAD = 2.0 * np.pi / 3.0 * 3.0  # rho (4 pi / 3) rc^3 / 2 at rho = 3
 OPS_PER_PAIR = 159   # displacement 6, r^2 + cutoff 4, r and w 3, e.v 7, Philox4x32-10 102,
 #                      Box-Muller 12, force magnitude 9, F on i and j 9, virial 7
@@ -361,6 +362,8 @@ def main():
     micro.close()
     if rank == 0 and not args.no_macro and args.uniform_edge <= 0:
         line["secondary"] = macro_step_rate()
+        from paper_2512_13267_gb300 import flows
+        line["rpf_paper"] = flows.rpf_paper_rate()
     if rank == 0 and not args.no_surrogate and args.uniform_edge <= 0:
         from paper_2512_13267_gb300 import closure
         r = closure.surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, n_eval=60)
@@ -368,7 +371,8 @@ def main():
             r.pop(k, None)
         r["metric"] = "LHMM macro-steps/s, surrogate-gated vs plain"
         r["budget"] = ("bench budget: 150 macro steps of training pairs (307k pairs), 2000 "
-                       "AdamW steps; the configs of DESIGN.md give the full-budget runs")
+                       "AdamW steps; full budget: closure.surrogate_vs_plain(n_data=500, "
+                       "train_steps=20000)")
         line["surrogate"] = r
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -14,8 +14,8 @@
  *   characteristic-stress scaling (Eq. pip); SPH momentum (Eq.
  *   sph_continuity), Tait EOS (Eq. tait), SPH velocity gradient
  *   (Eq. macro_micro), Lucy kernel (Appendix A).
- * Readings where the paper is silent or garbled are listed in the design doc and
- * repeated at the function that uses them.
+ * Readings where the paper is silent or garbled are stated at the top of
+ * each source file and at the function that uses them.
  */
 #ifndef LHMM_ORACLE_H
 #define LHMM_ORACLE_H

@@ -5,7 +5,7 @@
  * TEST INFRASTRUCTURE ONLY (see lhmm_oracle.h).  Plain loops, double
  * precision, no blocking or fusion beyond what the equations state.
  *
- * Readings of the paper used here (each is also listed in the design doc):
+ * Readings of the paper used here:
  *  R1 weight functions: w^R(r) = 1 - r/rc, w^D = (w^R)^2 (FDT, Sec. 2.3);
  *     the paper names the FDT relation but never prints w^R.
  *  R2 random force: F^R = sigma w^R theta_ij e_ij / sqrt(dt); the 1/sqrt(dt)

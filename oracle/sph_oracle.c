@@ -8,7 +8,7 @@
  * TEST INFRASTRUCTURE ONLY (see lhmm_oracle.h).  O(N^2) pair search with the
  * minimum image: obviously correct, slow.
  *
- * Readings (also in the design doc):
+ * Readings of the paper used here:
  *  S1 kernel: Wendland C2 in 2D with support radius h (default), or the Lucy
  *     kernel of Appendix A; F_IJ = -W'(r)/r.
  *  S2 d_I includes the self term W(0).

@@ -363,12 +363,12 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
     __syncthreads();
 
     // ---- C: forces and pair virial, each pair once (Newton's third law).
-    // Each lane owns one bead per round and scans the upper half of its
-    // neighbourhood: the rest of its own cell, the next x cell, and the rows
-    // (dz, dy) = (0,+1), (+1,-1), (+1,0), (+1,+1) of three x cells, each row
-    // one or two contiguous slot ranges.  Pairs inside r_c go to the warp's
-    // queue and are evaluated 32 at a time with every lane busy; f_i += F_ij
-    // and f_j -= F_ij with shared-memory atomics.
+    // A lane owns one bead of a work item and scans one row of the upper half
+    // of its neighbourhood (its own row after its slot, or one of the rows
+    // (dz, dy) = (0,+1), (+1,-1), (+1,0), (+1,+1)), cut to the x window that
+    // can hold partners within r_c.  Pairs inside r_c go to the warp's queue
+    // and are evaluated 32 at a time with every lane busy; f_i += F_ij and
+    // f_j -= F_ij with shared-memory atomics.
     float W[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     auto eval_pair = [&](unsigned long long e) {
       const int i = static_cast<int>(e & 0xffffu), j = static_cast<int>((e >> 16) & 0xffffu);

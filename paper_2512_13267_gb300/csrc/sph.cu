@@ -506,7 +506,7 @@ extern "C" lhmm_status lhmm_sph_get_state(lhmm_sph_t h, float* pos_host, float* 
 //
 // Some callers cannot call cudaMalloc at the point where they need this
 // result: code running inside another framework's memory pool or
-// allocator-free section, real-time loops that must not touch the driver's
+// allocator-free section, real-time loops that must not touch the CUDA
 // allocator, or plug-ins that may only use memory they are handed.  For them
 // this entry point computes the same SPH number densities and velocity
 // gradients as lhmm_sph_step(..., n_substeps = 0, L_out) but keeps all of its

@@ -31,14 +31,8 @@ def rpf_exact_shear_stress(y, F, Ly, rho=1.0):
     return np.where(y < 0.5 * Ly, F * rho * (0.25 * Ly - y), F * rho * (y - 0.75 * Ly))
 
 
-def rpf_paper(F=1e-3, chain_len=8, alpha=1e-4, n_macro=1000, n_avg=300, box_edge=20.0,
-              nbins=20, seed=3, c=0.25, eta_s=0.02, exclude_bonds=0, timing_steps=50,
-              dh=0.1, dt_sph=0.04):
-    """Run the coupled RPF of Sec. 6.1 and compare the time-averaged binned
-    total shear stress sigma_xy = eta_s (L_xy + L_yx) + pi_xy (pi as the SPH
-    momentum equation uses it) with -tau_xy of Eq. RPF over the last n_avg of
-    n_macro macro steps.  Returns the profiles, the relative L2 error, the
-    largest error over tau_max = F rho L_y / 4, and macro-steps/s."""
+def _rpf_system(F, chain_len, alpha, box_edge, seed, c, eta_s, exclude_bonds, dh, dt_sph):
+    """SPH particles, micro boxes and the coupled handle of the RPF set-up."""
     import torch
     Ly = Lx = 4.0
     n_side = int(round(Ly / dh))
@@ -61,6 +55,54 @@ def rpf_paper(F=1e-3, chain_len=8, alpha=1e-4, n_macro=1000, n_avg=300, box_edge
     L0 = torch.zeros((n, 9), dtype=torch.float32, device="cuda")
     micro.autotune(L0, probe_steps=8)
     cpl = lhmm.Coupled(sph, micro, M, k_micro)
+    return sph, micro, cpl, batch, M, k_micro, Ly
+
+
+def _rate(cpl, steps):
+    import torch
+    s = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    cpl.step(steps, use_graph=True)
+    e1.record(s)
+    e1.synchronize()
+    return steps / (e0.elapsed_time(e1) / 1e3)
+
+
+def rpf_paper_rate(steps=20, warmup=3, F=1e-3, chain_len=8, alpha=1e-4, box_edge=20.0, seed=3):
+    """Macro-steps/s of the paper's RPF set-up (graph-replayed macro steps
+    after `warmup` untimed ones), without the convergence run."""
+    sph, micro, cpl, batch, M, k_micro, _ = _rpf_system(F, chain_len, alpha, box_edge, seed, 0.25,
+                                                        0.02, 0, 0.1, 0.04)
+    cpl.step(warmup, use_graph=True)
+    rate = _rate(cpl, steps)
+    status = lhmm.status_string(micro.sync(raise_on_error=False)[0])
+    out = dict(metric="LHMM macro-steps/s (plain DPD closure), paper's RPF set-up",
+               value=rate, unit="macro-steps/s", steps=steps, warmup=warmup,
+               sph_particles=int(batch.n_boxes), sph_substeps=M, micro_steps=k_micro,
+               boxes=batch.n_boxes, beads=int(batch.total_beads),
+               bead_steps_per_s=rate * batch.total_beads * k_micro, device_status=status,
+               workload="reverse-Poiseuille 40x40 SPH (Lucy h=4dh, eta_s=0.02, dt_SPH=0.04) x "
+                        "2D N_d=%d melt boxes of %d beads (Table 1, AFBC), 64 DPD steps per "
+                        "macro step, F=%g" % (chain_len, int(batch.n_beads[0]), F))
+    for o in (cpl, micro, sph):
+        o.close()
+    return out
+
+
+def rpf_paper(F=1e-3, chain_len=8, alpha=1e-4, n_macro=1000, n_avg=300, box_edge=20.0,
+              nbins=20, seed=3, c=0.25, eta_s=0.02, exclude_bonds=0, timing_steps=50,
+              dh=0.1, dt_sph=0.04):
+    """Run the coupled RPF of Sec. 6.1 and compare the time-averaged binned
+    total shear stress sigma_xy = eta_s (L_xy + L_yx) + pi_xy (pi as the SPH
+    momentum equation uses it) with -tau_xy of Eq. RPF over the last n_avg of
+    n_macro macro steps.  Returns the profiles, the relative L2 error, the
+    largest error over tau_max = F rho L_y / 4, and macro-steps/s."""
+    sph, micro, cpl, batch, M, k_micro, Ly = _rpf_system(F, chain_len, alpha, box_edge, seed, c,
+                                                         eta_s, exclude_bonds, dh, dt_sph)
+    n = batch.n_boxes
+    nb = int(batch.n_beads[0])
     t0 = time.perf_counter()
     cpl.step(n_macro - n_avg, use_graph=True)
     edges = np.linspace(0.0, Ly, nbins + 1)
@@ -82,15 +124,7 @@ def rpf_paper(F=1e-3, chain_len=8, alpha=1e-4, n_macro=1000, n_avg=300, box_edge
     yc = 0.5 * (edges[1:] + edges[:-1])
     exact = -rpf_exact_shear_stress(yc, F, Ly)  # sigma_xy = -tau_xy
     tau_max = F * Ly / 4.0
-    # timing of graph-replayed macro steps alone
-    s = torch.cuda.current_stream()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(s)
-    cpl.step(timing_steps, use_graph=True)
-    e1.record(s)
-    e1.synchronize()
-    rate = timing_steps / (e0.elapsed_time(e1) / 1e3)
+    rate = _rate(cpl, timing_steps)
     status = lhmm.status_string(micro.sync(raise_on_error=False)[0])
     out = dict(F=F, chain_len=chain_len, alpha=alpha, particles=n, box_beads=nb,
                beads=int(batch.total_beads), sph_substeps=M, micro_steps=k_micro,
