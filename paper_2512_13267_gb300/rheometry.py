@@ -77,3 +77,88 @@ def melt_viscosity(chain_len, shear_rates, replicas=32, edge=20.0, equil_time=No
                 equil_steps=n_equil * call_steps, sample_steps=n_sample * call_steps,
                 bead_steps=int(batch.total_beads) * (n_equil + n_sample) * call_steps,
                 wall_s=wall, device_status=lhmm.status_string(status))
+
+
+def stress_relaxation(chain_len, shear_rate, replicas=64, edge=20.0, shear_time=None,
+                      relax_time=None, sample_time=1.0, seed=13, exclude_bonds=0):
+    """Recovery test (Sec. 5.2): steady shear at shear_rate for shear_time,
+    then the shear is removed and the replica-averaged pi_xy is recorded in
+    windows of sample_time; G(t) = <pi_xy(t)> / gamma with gamma the total
+    applied strain shear_rate * shear_time (the paper's definition)."""
+    import torch
+    dt = PAPER_2D["dt"]
+    lam_guess = 23.5 * (chain_len / 4.0) ** 2
+    shear_time = max(100.0, 5 * lam_guess) if shear_time is None else shear_time
+    relax_time = max(100.0, 5 * lam_guess) if relax_time is None else relax_time
+    batch = synth.melt_rheometer_batch(chain_len, [shear_rate], replicas, edge=edge, seed=seed)
+    params = lhmm.dpd_params(flow="lees_edwards", seed=seed, dim=2, exclude_bonds=exclude_bonds,
+                             **PAPER_2D)
+    m = lhmm.Micro.from_batch(params, batch)
+    L = torch.from_numpy(batch.L).cuda()
+    st = torch.zeros((batch.n_boxes, 6), dtype=torch.float64, device="cuda")
+    chunk = 1000
+    n_shear = int(np.ceil(shear_time / dt / chunk))
+    for _ in range(n_shear):
+        m.advance(L, chunk, st)
+    sheared = st.mean(dim=0).cpu().numpy()
+    L0 = torch.zeros_like(L)
+    k = max(1, int(round(sample_time / dt)))
+    n_rel = int(np.ceil(relax_time / (k * dt)))
+    t, pxy, se = [], [], []
+    for s in range(n_rel):
+        m.advance(L0, k, st)
+        x = st[:, 3].cpu().numpy()
+        t.append((s + 0.5) * k * dt)
+        pxy.append(float(x.mean()))
+        se.append(float(x.std(ddof=1) / np.sqrt(len(x))))
+    status = lhmm.status_string(m.sync(raise_on_error=False)[0])
+    m.close()
+    gamma = shear_rate * n_shear * chunk * dt
+    return dict(chain_len=chain_len, shear_rate=shear_rate, replicas=replicas, edge=edge,
+                strain=gamma, steady_pi_xy=float(sheared[3]), t=t, pi_xy=pxy, pi_xy_se=se,
+                G=[p / gamma for p in pxy], device_status=status)
+
+
+def planar_extension(chain_len, rates, replicas=32, edge=36.0, equil_time=None,
+                     sample_time=None, call_steps=1000, seed=17, exclude_bonds=0):
+    """Steady planar extension L = diag(e, -e) imposed through the AFBC shell
+    of 2D melt boxes; planar extensional viscosity eta_P = (pi_xx - pi_yy)/e
+    from the core's IK stress.  For a Newtonian liquid eta_P = 4 eta (the
+    planar Trouton ratio), the low-rate check against the shear viscosity."""
+    import torch
+    rates = np.asarray(rates, dtype=np.float64)
+    dt = PAPER_2D["dt"]
+    lam_guess = 23.5 * (chain_len / 4.0) ** 2
+    equil_time = max(100.0, 5 * lam_guess) if equil_time is None else equil_time
+    sample_time = max(200.0, 10 * lam_guess) if sample_time is None else sample_time
+    e = np.repeat(rates, int(replicas))
+    B = e.shape[0]
+    L = np.zeros((B, 9), np.float32)
+    L[:, 0] = e
+    L[:, 4] = -e
+    n = int(round(synth.DENSITY_PAPER_2D * edge * edge))
+    n -= n % chain_len
+    batch = synth.make_batch(np.full(B, edge), L, seed, flow="afbc", chain_len=chain_len,
+                             fraction=1.0, n_beads=np.full(B, n), dim=2)
+    params = lhmm.dpd_params(flow="afbc", seed=seed, dim=2, exclude_bonds=exclude_bonds,
+                             **PAPER_2D)
+    t0 = time.perf_counter()
+    m = lhmm.Micro.from_batch(params, batch)
+    Ld = torch.from_numpy(L).cuda()
+    st = torch.zeros((B, 6), dtype=torch.float64, device="cuda")
+    acc = torch.zeros_like(st)
+    n_equil = int(np.ceil(equil_time / dt / call_steps))
+    n_sample = int(np.ceil(sample_time / dt / call_steps))
+    for _ in range(n_equil):
+        m.advance(Ld, call_steps, st)
+    for _ in range(n_sample):
+        m.advance(Ld, call_steps, st)
+        acc += st
+    status = lhmm.status_string(m.sync(raise_on_error=False)[0])
+    mean = (acc / n_sample).cpu().numpy().reshape(len(rates), replicas, 6)
+    etaP = (mean[:, :, 0] - mean[:, :, 1]) / rates[:, None]
+    m.close()
+    return dict(chain_len=chain_len, rates=rates.tolist(), replicas=replicas, edge=edge,
+                beads_per_box=n, eta_P=etaP.mean(axis=1).tolist(),
+                eta_P_se=(etaP.std(axis=1, ddof=1) / np.sqrt(replicas)).tolist(),
+                wall_s=time.perf_counter() - t0, device_status=status)
