@@ -223,6 +223,107 @@ def surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, batch=4096, n_eval
     return out
 
 
+def _cylinder_system(n_fluid, cell, box_beads, U_o, c_factor, eta_s, alpha, k_micro, dt_dpd,
+                     seed):
+    """The large mixed workload: cylinder-array SPH particles with walls and
+    one AFBC box per fluid particle, coupled (autotuned launches)."""
+    import torch
+    from . import synth
+    pos, is_wall, L, dh = synth.cylinder_array(n_fluid_target=n_fluid, radius_frac=0.25, cell=cell)
+    n = pos.shape[0]
+    n_wall = int(is_wall.sum())
+    eta_tot = eta_s + 0.01
+    F = 48.0 * eta_tot * U_o / L ** 2
+    c = c_factor * U_o
+    delta_t = k_micro * dt_dpd
+    dt_cfl = 0.25 * min(dh / (1.5 * U_o + c), np.sqrt(dh / F), dh * dh / (2.0 * eta_tot))
+    M = int(np.ceil(delta_t / dt_cfl))
+    sp = lhmm.sph_params(n, n_wall, Lx=L, Ly=L, h=3 * dh, mass=dh * dh, rho0=1.0, c=c,
+                         theta_pb=0.1, eta_s=eta_s, dt=delta_t / M, body_force=(F, 0.0),
+                         body_mode=lhmm.SPH_BODY_UNIFORM)
+    sph = lhmm.Sph(sp, pos, np.zeros_like(pos))
+    edge = (box_beads / synth.DENSITY) ** (1.0 / 3.0)
+    batch = synth.make_batch(np.full(n_fluid, edge), np.zeros((n_fluid, 9), np.float32), seed,
+                             flow="afbc", n_beads=np.full(n_fluid, box_beads))
+    micro = lhmm.Micro.from_batch(lhmm.dpd_params(flow="afbc", seed=seed, alpha=alpha), batch)
+    L0 = torch.zeros((n_fluid, 9), dtype=torch.float32, device="cuda")
+    micro.autotune(L0, probe_steps=5)
+    cpl = lhmm.Coupled(sph, micro, M, k_micro)
+    return cpl, sph, micro, batch, L, M, n_wall
+
+
+def large_mixed_accuracy(n_fluid=16384, cell=16.0, box_beads=1000, U_o=0.25, c_factor=10.0,
+                         eta_s=0.1, alpha=0.01, k_micro=50, dt_dpd=0.01, seed=5, warm=20,
+                         n_data=60, train_steps=4000, n_eval=100, threshold=0.02,
+                         audit_every=50, absolute=False, noise_floor=True, nbins=8,
+                         timing_steps=50, weight_decay=0.0):
+    """Surrogate-gated vs plain on the large mixed workload: two identical
+    systems (and, with noise_floor, a third plain one with another seed) run
+    the same plain steps; one collects pairs and trains its closure; then all
+    run n_eval steps and the time-averaged pi_xy and N1 fields, binned on an
+    nbins x nbins grid over the cell (fluid particles), are compared.
+    Returns errors, DPD share and rates."""
+    kw = dict(n_fluid=n_fluid, cell=cell, box_beads=box_beads, U_o=U_o, c_factor=c_factor,
+              eta_s=eta_s, alpha=alpha, k_micro=k_micro, dt_dpd=dt_dpd)
+    A, sphA, microA, batch, Lc, M, n_wall = _cylinder_system(seed=seed, **kw)
+    B, sphB, microB, _, _, _, _ = _cylinder_system(seed=seed, **kw)
+    systems = [("A", A, sphA), ("B", B, sphB)]
+    objs = [A, microA, sphA, B, microB, sphB]
+    if noise_floor:
+        Cc, sphC, microC, _, _, _, _ = _cylinder_system(seed=seed + 1000, **kw)
+        systems.append(("C", Cc, sphC))
+        objs += [Cc, microC, sphC]
+    clo = lhmm.Closure(members=5, in_dim=N_IN, hidden=256, n_hidden=4, out_dim=N_OUT, seed=seed)
+    objs.append(clo)
+    B.set_closure(clo, threshold=threshold, audit_every=audit_every)
+    B.set_gate(threshold, audit_every, absolute)
+    for name, sysm, _ in systems:
+        if name != "B":
+            sysm.step(warm + n_data, use_graph=True)
+    B.step(warm, use_graph=True)
+    X, T = collect_pairs(B, n_data, skip=0, absolute=absolute)
+    mean, std, scale = normalization(X, T)
+    clo.set_normalization(mean, std, scale)
+    _, t_train = train(clo, X, T, train_steps, weight_decay=weight_decay)
+    B.enable_gate(True)
+    g0 = B.gate_stats()
+    nf = n_fluid
+    acc = {name: np.zeros((2, nbins * nbins)) for name, _, _ in systems}
+    for _ in range(n_eval):
+        for name, sysm, sph in systems:
+            sysm.step(1, use_graph=True)
+            p = sph.get_state()[0][:nf]
+            _, st = sysm.exchange()
+            ix = np.minimum((p[:, 0] / Lc * nbins).astype(int), nbins - 1)
+            iy = np.minimum((p[:, 1] / Lc * nbins).astype(int), nbins - 1)
+            k = ix + nbins * iy
+            cnt = np.maximum(np.bincount(k, minlength=nbins * nbins), 1)
+            acc[name][0] += np.bincount(k, weights=st[:, 3], minlength=nbins * nbins) / cnt / n_eval
+            acc[name][1] += np.bincount(k, weights=st[:, 0] - st[:, 1],
+                                        minlength=nbins * nbins) / cnt / n_eval
+    g1 = B.gate_stats()
+    rate_gated = _rate(B, timing_steps)
+    rate_plain = _rate(A, timing_steps)
+    out = dict(workload="periodic cylinder array, %d fluid + %d wall SPH particles, %d-bead AFBC "
+                        "boxes, k'=%d, M=%d" % (n_fluid, n_wall, box_beads, k_micro, M),
+               target="stress" if absolute else "increment", threshold=threshold,
+               train_pairs=int(X.shape[0]), train_steps=train_steps, t_train_s=t_train,
+               n_eval=n_eval, nbins=nbins,
+               stress_error_pxy=rel_l2(acc["B"][0], acc["A"][0]),
+               stress_error_n1=rel_l2(acc["B"][1], acc["A"][1]),
+               dpd_fraction=(g1["dpd_boxes"] - g0["dpd_boxes"])
+               / max(1, (g1["gated_steps"] - g0["gated_steps"]) * nf),
+               macro_steps_per_s_plain=rate_plain, macro_steps_per_s_surrogate=rate_gated,
+               speedup=rate_gated / rate_plain,
+               device_status=lhmm.status_string(microB.sync(raise_on_error=False)[0]))
+    if noise_floor:
+        out["noise_floor_pxy"] = rel_l2(acc["C"][0], acc["A"][0])
+        out["noise_floor_n1"] = rel_l2(acc["C"][1], acc["A"][1])
+    for o in objs:
+        o.close()
+    return out
+
+
 def large_mixed_run(n_fluid=16384, cell=16.0, box_beads=1000, U_o=0.25, c_factor=10.0,
                     eta_s=0.1, alpha=0.01, k_micro=50, dt_dpd=0.01, seed=5, warm=10, n_data=30,
                     train_steps=2000, timing_steps=10, threshold=0.02, audit_every=50):

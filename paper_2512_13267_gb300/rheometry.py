@@ -120,11 +120,15 @@ def stress_relaxation(chain_len, shear_rate, replicas=64, edge=20.0, shear_time=
 
 
 def planar_extension(chain_len, rates, replicas=32, edge=36.0, equil_time=None,
-                     sample_time=None, call_steps=1000, seed=17, exclude_bonds=0):
+                     sample_time=None, call_steps=1000, seed=17, exclude_bonds=0,
+                     mode="extension"):
     """Steady planar extension L = diag(e, -e) imposed through the AFBC shell
     of 2D melt boxes; planar extensional viscosity eta_P = (pi_xx - pi_yy)/e
     from the core's IK stress.  For a Newtonian liquid eta_P = 4 eta (the
-    planar Trouton ratio), the low-rate check against the shear viscosity."""
+    planar Trouton ratio), the low-rate check against the shear viscosity.
+    mode = "shear" imposes simple shear L_xy = rate through the same AFBC
+    shell instead and returns eta = pi_xy / rate as eta_P (to set against the
+    Lees-Edwards rheometer)."""
     import torch
     rates = np.asarray(rates, dtype=np.float64)
     dt = PAPER_2D["dt"]
@@ -134,8 +138,11 @@ def planar_extension(chain_len, rates, replicas=32, edge=36.0, equil_time=None,
     e = np.repeat(rates, int(replicas))
     B = e.shape[0]
     L = np.zeros((B, 9), np.float32)
-    L[:, 0] = e
-    L[:, 4] = -e
+    if mode == "shear":
+        L[:, 1] = e
+    else:
+        L[:, 0] = e
+        L[:, 4] = -e
     n = int(round(synth.DENSITY_PAPER_2D * edge * edge))
     n -= n % chain_len
     batch = synth.make_batch(np.full(B, edge), L, seed, flow="afbc", chain_len=chain_len,
@@ -156,9 +163,12 @@ def planar_extension(chain_len, rates, replicas=32, edge=36.0, equil_time=None,
         acc += st
     status = lhmm.status_string(m.sync(raise_on_error=False)[0])
     mean = (acc / n_sample).cpu().numpy().reshape(len(rates), replicas, 6)
-    etaP = (mean[:, :, 0] - mean[:, :, 1]) / rates[:, None]
+    if mode == "shear":
+        etaP = mean[:, :, 3] / rates[:, None]
+    else:
+        etaP = (mean[:, :, 0] - mean[:, :, 1]) / rates[:, None]
     m.close()
     return dict(chain_len=chain_len, rates=rates.tolist(), replicas=replicas, edge=edge,
-                beads_per_box=n, eta_P=etaP.mean(axis=1).tolist(),
+                mode=mode, beads_per_box=n, eta_P=etaP.mean(axis=1).tolist(),
                 eta_P_se=(etaP.std(axis=1, ddof=1) / np.sqrt(replicas)).tolist(),
                 wall_s=time.perf_counter() - t0, device_status=status)
