@@ -371,10 +371,14 @@ lhmm_status lhmm_coupled_enable_gate(lhmm_coupled_t c, int enabled);
  * predicts the stress itself from the gradient history alone (the three
  * stress inputs are written as zero), a trusted particle takes pi =
  * prediction, and the relative spread is taken against the predicted stress.
- * Other values return LHMM_ERR_ARG.  The next macro step re-captures its
- * graph.  Synchronous. */
+ * Other values return LHMM_ERR_ARG.  warmup_steps: a box that was frozen
+ * (trusted) in the previous gated macro step and runs DPD in this one first
+ * runs warmup_steps DPD steps under the current gradient whose stress is
+ * discarded, then the k' sampled steps; -1 means k' (the default after
+ * set_closure), 0 resumes at once; below -1 returns LHMM_ERR_ARG.  The next
+ * macro step re-captures its graph.  Synchronous. */
 lhmm_status lhmm_coupled_set_gate(lhmm_coupled_t c, float threshold, int audit_every,
-                                  int absolute);
+                                  int absolute, int warmup_steps);
 /* Counters since the closure was attached: gated macro steps, boxes advanced
  * by DPD in them, audited boxes, and over the audited boxes the summed squared
  * error of the predicted increment and the summed squared DPD increment.

@@ -79,6 +79,34 @@ def train(closure, X, T, steps, batch=4096, lr=1e-3, weight_decay=1e-4, seed=0, 
     return hist, time.perf_counter() - t0
 
 
+def calibrate(closure, X_val, T_val, out_scale):
+    """Per-output linear recalibration of the ensemble mean on held-out pairs:
+    fit T ~ a * prediction + c by least squares and fold (a, c) into every
+    member's output layer (W_out row k times a_k, b_out[k] -> a_k b_out[k] +
+    c_k / out_scale_k).  Returns (a, c)."""
+    import torch
+    Xd = torch.from_numpy(np.ascontiguousarray(X_val, np.float32)).cuda()
+    Y = closure.forward_members(Xd).mean(axis=0) * np.asarray(out_scale)[None, :]
+    a = np.ones(closure.out_dim)
+    c = np.zeros(closure.out_dim)
+    for k in range(closure.out_dim):
+        A = np.stack([Y[:, k], np.ones(len(Y))], axis=1).astype(np.float64)
+        sol, *_ = np.linalg.lstsq(A, T_val[:, k].astype(np.float64), rcond=None)
+        a[k], c[k] = sol
+    d_hidden = closure.dims[-2]
+    for m in range(closure.members):
+        prm = closure.get_params(m).astype(np.float64)
+        b0 = prm.size - closure.out_dim
+        w0 = b0 - closure.out_dim * d_hidden
+        W = prm[w0:b0].reshape(closure.out_dim, d_hidden)
+        b = prm[b0:]
+        W *= a[:, None]
+        prm[w0:b0] = W.ravel()
+        prm[b0:] = a * b + c / np.asarray(out_scale, np.float64)
+        closure.set_params(m, prm.astype(np.float32))
+    return a, c
+
+
 def binned_profiles(y, stress6, Ly, nbins=16):
     """y-binned pi_xy and N1 = pi_xx - pi_yy of the fluid particles."""
     k = np.minimum((np.asarray(y) / Ly * nbins).astype(int), nbins - 1)
@@ -128,7 +156,7 @@ def surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, batch=4096, n_eval
                        threshold=0.02, audit_every=50, timing_steps=10, seed=3, alpha=0.01,
                        U_o=0.25, c_factor=10.0, eta_s=0.1, k_micro=50, dt_dpd=0.01, members=5,
                        lr=1e-3, weight_decay=1e-4, cosine=False, nbins=16, thresholds=None,
-                       noise_floor=False, absolute=False):
+                       noise_floor=False, absolute=False, warmup_steps=-1, calibrated=False):
     """Plain LHMM vs surrogate-gated LHMM on the coupled reverse-Poiseuille
     channel.  Two identical systems run the same `warm + n_data` plain steps
     (one collects training pairs); the ensemble trains on the GPU; then both run
@@ -152,7 +180,7 @@ def surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, batch=4096, n_eval
         systems.append(("C", C))
     A.set_closure(clo_a, threshold=threshold, audit_every=audit_every)
     B.set_closure(clo_b, threshold=threshold, audit_every=audit_every)
-    B.set_gate(threshold, audit_every, absolute)
+    B.set_gate(threshold, audit_every, absolute, warmup_steps)
     t0 = time.perf_counter()
     A.step(warm + n_data, use_graph=True)
     if C is not None:
@@ -160,16 +188,21 @@ def surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, batch=4096, n_eval
     B.step(warm, use_graph=True)
     X, T = collect_pairs(B, n_data, skip=0, absolute=absolute)
     t_data = time.perf_counter() - t0
-    mean, std, scale = normalization(X, T)
+    n_fit = X.shape[0] if not calibrated else (X.shape[0] * 9 // 10)  # last 10 %: calibration
+    mean, std, scale = normalization(X[:n_fit], T[:n_fit])
     clo_b.set_normalization(mean, std, scale)
-    hist, t_train = train(clo_b, X, T, train_steps, batch=batch, lr=lr,
+    hist, t_train = train(clo_b, X[:n_fit], T[:n_fit], train_steps, batch=batch, lr=lr,
                           weight_decay=weight_decay, log_every=max(1, train_steps // 10),
                           cosine=cosine)
+    calib = None
+    if calibrated:
+        a_c, c_c = calibrate(clo_b, X[n_fit:], T[n_fit:], scale)
+        calib = dict(a=a_c.tolist(), c=c_c.tolist())
     B.enable_gate(True)
     Ly = cfg["Ly"]
     windows = []
     for thr in (thresholds if thresholds else [threshold]):
-        B.set_gate(thr, audit_every, absolute)
+        B.set_gate(thr, audit_every, absolute, warmup_steps)
         acc = {name: [np.zeros(nbins), np.zeros(nbins)] for name, _ in systems}
         g_before = B.gate_stats()
         for _ in range(n_eval):
@@ -212,7 +245,7 @@ def surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, batch=4096, n_eval
         train_loss_last=[float(x) for x in hist[-1]] if hist else None,
         t_data_s=t_data, t_train_s=t_train, sph_substeps=M, micro_steps=k_micro,
         boxes=B.n_boxes, threshold=last["threshold"], audit_every=audit_every, n_eval=n_eval,
-        target="stress" if absolute else "increment",
+        target="stress" if absolute else "increment", calibration=calib,
         windows=windows if len(windows) > 1 else None,
         noise_floor_pxy=last.get("noise_floor_pxy"), noise_floor_n1=last.get("noise_floor_n1"),
         profile_pxy_plain=last["profile_pxy_plain"],
@@ -256,7 +289,7 @@ def large_mixed_accuracy(n_fluid=16384, cell=16.0, box_beads=1000, U_o=0.25, c_f
                          eta_s=0.1, alpha=0.01, k_micro=50, dt_dpd=0.01, seed=5, warm=20,
                          n_data=60, train_steps=4000, n_eval=100, threshold=0.02,
                          audit_every=50, absolute=False, noise_floor=True, nbins=8,
-                         timing_steps=50, weight_decay=0.0):
+                         timing_steps=50, weight_decay=0.0, warmup_steps=-1):
     """Surrogate-gated vs plain on the large mixed workload: two identical
     systems (and, with noise_floor, a third plain one with another seed) run
     the same plain steps; one collects pairs and trains its closure; then all
@@ -276,7 +309,7 @@ def large_mixed_accuracy(n_fluid=16384, cell=16.0, box_beads=1000, U_o=0.25, c_f
     clo = lhmm.Closure(members=5, in_dim=N_IN, hidden=256, n_hidden=4, out_dim=N_OUT, seed=seed)
     objs.append(clo)
     B.set_closure(clo, threshold=threshold, audit_every=audit_every)
-    B.set_gate(threshold, audit_every, absolute)
+    B.set_gate(threshold, audit_every, absolute, warmup_steps)
     for name, sysm, _ in systems:
         if name != "B":
             sysm.step(warm + n_data, use_graph=True)

@@ -20,6 +20,8 @@ struct GateState {
   float floor = 1e-3f;      // stress scale floor of the relative spread
   int audit_every = 50;     // every audit_every-th trusted box (round robin) runs DPD anyway
   int absolute = 0;         // 0: closure predicts the increment of pi; 1: pi itself
+  int warmup = -1;          // DPD steps a box frozen in the last gated step runs before its
+                            // sampled ones when it comes back (-1: the coupling interval k')
   int enabled = 0;
   float* hist = nullptr;    // n x kHist x 4 ring of (Lxx, Lxy, Lyx, Lyy)
   float* X = nullptr;       // n x kFeat closure inputs
@@ -32,6 +34,10 @@ struct GateState {
   unsigned char* audited = nullptr;  // n
   float* pred = nullptr;    // n x 3 prediction of audited boxes
   float* before = nullptr;  // n x 3 stress before the step of audited boxes
+  unsigned char* frozen = nullptr;  // n: box was trusted (not advanced) in the last gated step
+  int* resume = nullptr;    // n box list of frozen boxes that run DPD this step
+  int* n_resume = nullptr;  // device count of that list
+  double* scratch = nullptr;  // n x 6 stress output of the warm-up (discarded)
 };
 
 struct lhmm_coupled_s {
@@ -82,7 +88,8 @@ __global__ void advance_ring(long long* counters) { counters[3] += 1; }
 __global__ void gate_select(const float* mean, const float* spread, double* stress, int n,
                             float thr, float floor_, int audit_every, int absolute,
                             long long* counters, int* active, int* n_active,
-                            unsigned char* audited, float* pred, float* before) {
+                            unsigned char* audited, float* pred, float* before,
+                            unsigned char* frozen, int* resume, int* n_resume) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= n) return;
   double* s = stress + 6 * static_cast<long long>(I);
@@ -98,6 +105,8 @@ __global__ void gate_select(const float* mean, const float* spread, double* stre
   const bool audit = trust && audit_every > 0 && ((I + step) % audit_every) == 0;
   if (!trust || audit) {
     active[atomicAdd(n_active, 1)] = I;
+    if (frozen[I]) resume[atomicAdd(n_resume, 1)] = I;  // stale box: warm up first
+    frozen[I] = 0;
     if (audit) {
       audited[I] = 1;
       pred[3 * I] = dxx;
@@ -108,6 +117,7 @@ __global__ void gate_select(const float* mean, const float* spread, double* stre
       before[3 * I + 2] = byy;
     }
   } else {
+    frozen[I] = 1;
     s[0] = static_cast<double>(bxx) + dxx;
     s[3] = static_cast<double>(bxy) + dxy;
     s[1] = static_cast<double>(byy) + dyy;
@@ -143,16 +153,24 @@ lhmm_status enqueue_macro_step(lhmm_coupled_s* c, cudaStream_t s, bool gated) {
     LHMM_CK(cudaGetLastError());
   }
   if (!gated) {
+    if (g.closure) LHMM_CK(cudaMemsetAsync(g.frozen, 0, static_cast<size_t>(n), s));  // all advance
     return lhmm_micro_advance(c->micro, c->L_d, nullptr, n, c->micro_steps, c->stress_d, nullptr, s);
   }
   st = lhmm_closure_infer(g.closure, g.X, n, g.mean, g.spread, s);
   if (st != LHMM_OK) return st;
   LHMM_CK(cudaMemsetAsync(g.n_active, 0, sizeof(int), s));
+  LHMM_CK(cudaMemsetAsync(g.n_resume, 0, sizeof(int), s));
   gate_select<<<G, T, 0, s>>>(g.mean, g.spread, c->stress_d, n, g.threshold, g.floor, g.audit_every,
                               g.absolute, g.counters, g.active, g.n_active, g.audited, g.pred,
-                              g.before);
+                              g.before, g.frozen, g.resume, g.n_resume);
   gate_tally<<<1, 1, 0, s>>>(g.counters, g.n_active);
   LHMM_CK(cudaGetLastError());
+  const int warm = g.warmup < 0 ? c->micro_steps : g.warmup;
+  if (warm > 0) {  // boxes back from a frozen state relax under the current gradient first
+    st = lhmm_micro_advance_dev_count(c->micro, c->L_d, g.resume, g.n_resume, n, warm, g.scratch,
+                                      nullptr, s);
+    if (st != LHMM_OK) return st;
+  }
   st = lhmm_micro_advance_dev_count(c->micro, c->L_d, g.active, g.n_active, n, c->micro_steps,
                                     c->stress_d, nullptr, s);
   if (st != LHMM_OK) return st;
@@ -173,6 +191,10 @@ void free_gate(GateState& g) {
   cudaFree(g.audited);
   cudaFree(g.pred);
   cudaFree(g.before);
+  cudaFree(g.frozen);
+  cudaFree(g.resume);
+  cudaFree(g.n_resume);
+  cudaFree(g.scratch);
   g = GateState();
 }
 
@@ -298,6 +320,11 @@ extern "C" lhmm_status lhmm_coupled_set_closure(lhmm_coupled_t c, lhmm_closure_t
       (e = cudaMalloc(&g.audited, n)) != cudaSuccess ||
       (e = cudaMalloc(&g.pred, sizeof(float) * n * 3)) != cudaSuccess ||
       (e = cudaMalloc(&g.before, sizeof(float) * n * 3)) != cudaSuccess ||
+      (e = cudaMalloc(&g.frozen, n)) != cudaSuccess ||
+      (e = cudaMalloc(&g.resume, sizeof(int) * n)) != cudaSuccess ||
+      (e = cudaMalloc(&g.n_resume, sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&g.scratch, sizeof(double) * n * 6)) != cudaSuccess ||
+      (e = cudaMemset(g.frozen, 0, n)) != cudaSuccess ||
       (e = cudaMemset(g.hist, 0, sizeof(float) * n * kHist * 4)) != cudaSuccess ||
       (e = cudaMemset(g.counters, 0, sizeof(long long) * 4)) != cudaSuccess ||
       (e = cudaMemset(g.audit, 0, sizeof(double) * 2)) != cudaSuccess ||
@@ -315,15 +342,16 @@ extern "C" lhmm_status lhmm_coupled_set_closure(lhmm_coupled_t c, lhmm_closure_t
 }
 
 extern "C" lhmm_status lhmm_coupled_set_gate(lhmm_coupled_t c, float threshold, int audit_every,
-                                             int absolute) {
+                                             int absolute, int warmup_steps) {
   if (!c || !c->gate.closure || !(threshold >= 0.f) || audit_every < 0 ||
-      (absolute != 0 && absolute != 1))
+      (absolute != 0 && absolute != 1) || warmup_steps < -1)
     return LHMM_ERR_ARG;
   LHMM_CK(cudaDeviceSynchronize());
   drop_graphs(c);  // the gate's launch arguments are baked into the captured graph
   c->gate.threshold = threshold;
   c->gate.audit_every = audit_every;
   c->gate.absolute = absolute;
+  c->gate.warmup = warmup_steps;
   return LHMM_OK;
 }
 

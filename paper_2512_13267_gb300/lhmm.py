@@ -101,7 +101,7 @@ def lib():
         L.lhmm_coupled_copy_exchange.argtypes = [vp, _F, _D]
         L.lhmm_coupled_set_closure.argtypes = [vp, vp, C.c_float, C.c_float, C.c_int]
         L.lhmm_coupled_enable_gate.argtypes = [vp, C.c_int]
-        L.lhmm_coupled_set_gate.argtypes = [vp, C.c_float, C.c_int, C.c_int]
+        L.lhmm_coupled_set_gate.argtypes = [vp, C.c_float, C.c_int, C.c_int, C.c_int]
         L.lhmm_coupled_gate_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                               C.POINTER(C.c_int64), _D, _D]
         L.lhmm_coupled_closure_inputs.argtypes = [vp, _F]
@@ -391,9 +391,10 @@ class Coupled:
     def enable_gate(self, on=True):
         check(lib().lhmm_coupled_enable_gate(self.h, int(bool(on))), "lhmm_coupled_enable_gate")
 
-    def set_gate(self, threshold, audit_every=50, absolute=False):
+    def set_gate(self, threshold, audit_every=50, absolute=False, warmup_steps=-1):
         check(lib().lhmm_coupled_set_gate(self.h, float(threshold), int(audit_every),
-                                          int(bool(absolute))), "lhmm_coupled_set_gate")
+                                          int(bool(absolute)), int(warmup_steps)),
+              "lhmm_coupled_set_gate")
 
     def gate_stats(self):
         a, b_, c_ = C.c_int64(), C.c_int64(), C.c_int64()

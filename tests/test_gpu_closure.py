@@ -119,3 +119,22 @@ def test_ensemble_mean_and_spread():
     sd = np.sqrt(((Y - Y.mean(axis=0)) ** 2).sum(axis=2).sum(axis=0) / 4)
     assert np.allclose(spread.cpu().numpy(), sd, rtol=1e-4, atol=1e-5)
     c.close()
+
+
+def test_calibration_folds_linear_map_into_output_layer():
+    from paper_2512_13267_gb300 import closure as CL
+    c = _closure(members=3, seed=17)
+    scale = np.array([2.0, 0.5, 3.0], np.float32)
+    c.set_normalization(np.zeros(67), np.ones(67), scale)
+    rng = np.random.default_rng(5)
+    X = rng.normal(size=(512, 67)).astype(np.float32)
+    Xd = torch.from_numpy(X).cuda()
+    P = c.forward_members(Xd).mean(axis=0) * scale
+    T = (np.array([1.5, -0.7, 2.0]) * P + np.array([0.3, 0.1, -0.2])).astype(np.float32)
+    a, b = CL.calibrate(c, X, T, scale)
+    assert np.allclose(a, [1.5, -0.7, 2.0], rtol=1e-3) and np.allclose(b, [0.3, 0.1, -0.2], atol=1e-3)
+    mean = torch.zeros((512, 3), dtype=torch.float32, device="cuda")
+    spread = torch.zeros(512, dtype=torch.float32, device="cuda")
+    c.infer(Xd, mean, spread)
+    assert np.allclose(mean.cpu().numpy(), T, rtol=2e-3, atol=2e-3 * np.abs(T).max())
+    c.close()

@@ -135,3 +135,22 @@ def test_absolute_mode_sets_stress_to_prediction():
     assert np.allclose(st1[:, [0, 3, 1]], mean.cpu().numpy(), rtol=1e-6, atol=1e-9)
     assert np.array_equal(st1[:, [2, 4, 5]], st0[:, [2, 4, 5]])
     assert cpl.gate_stats()["dpd_boxes"] == 0
+
+
+@pytest.mark.parametrize("warm,expect_extra", [(-1, 6), (0, 0), (3, 3)])
+def test_frozen_boxes_warm_up_when_they_return(warm, expect_extra):
+    # boxes frozen by the gate run `warm` discarded DPD steps (-1: k' = 6)
+    # before their sampled k' steps when the gate sends them back to DPD
+    cpl, clo = _system(seed=19)
+    cpl.set_closure(clo, threshold=1e30, audit_every=0)
+    cpl.step(17, use_graph=True)
+    cpl.enable_gate(True)
+    cpl.step(1, use_graph=False)          # every box trusted: all frozen
+    before = [cpl.micro.get_state(b)[3] for b in range(cpl.n_boxes)]
+    cpl.set_gate(0.0, 0, warmup_steps=warm)  # now every box runs DPD
+    cpl.step(1, use_graph=False)
+    after = [cpl.micro.get_state(b)[3] for b in range(cpl.n_boxes)]
+    assert all(a - b == 6 + expect_extra for a, b in zip(after, before))
+    cpl.step(1, use_graph=False)          # no box was frozen in between: no warm-up
+    again = [cpl.micro.get_state(b)[3] for b in range(cpl.n_boxes)]
+    assert all(a - b == 6 for a, b in zip(again, after))
