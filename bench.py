@@ -366,7 +366,8 @@ def main():
         line["rpf_paper"] = flows.rpf_paper_rate()
     if rank == 0 and not args.no_surrogate and args.uniform_edge <= 0:
         from paper_2512_13267_gb300 import closure
-        r = closure.surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, n_eval=60)
+        r = closure.surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, n_eval=60,
+                                       absolute=True, calibrated=True, weight_decay=0.0)
         for k in ("profile_pxy_plain", "profile_pxy_surrogate"):
             r.pop(k, None)
         r["metric"] = "LHMM macro-steps/s, surrogate-gated vs plain"
