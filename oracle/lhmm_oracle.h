@@ -57,6 +57,9 @@ typedef struct {
                          one cell layer, no z neighbours); volumes become areas */
   int exclude_bonds;  /* K in 0..3: no DPD pair force between beads of one chain at
                          most K bonds apart (dpd_on_bonded = 0 means at least 1) */
+  int afbc_mode;      /* 0: BC beads take v = L r' (R8); 1: they keep their peculiar
+                         velocity about the mean of the BC beads of their cell,
+                         v = L r' + (v - mean_cell(v)) (R8's alternative) */
 } orc_dpd_params;
 
 typedef struct {

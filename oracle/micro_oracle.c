@@ -24,6 +24,8 @@
  *  R8 AFBC: concentric cubic shells by fraction of the edge (Table 2), region
  *     by max-norm distance from the box centre; after the second half kick
  *     every BC bead gets v = L r' (Eq. micro_bc), r' relative to the centre.
+ *     Alternative (afbc_mode = 1): v = L r' + (v - mean of the BC beads of
+ *     the bead's cell), keeping the thermal motion of the shell.
  *  R9 IK: uniform weight w_IK = 1/V_core on the core; the bond function is
  *     the length fraction of segment i->j inside the core over V_core.
  *     Sign: pi = -(sum m dv(x)dv + sum_{i<j} F_ij (x) r_ij)/V_core, i.e.
@@ -424,7 +426,40 @@ int orc_advance(const orc_dpd_params* p, orc_box* b, const double L[9], int n_st
     double v6[6];
     err |= orc_compute_forces(p, b, L, 0, v6);
     for (int k = 0; k < 3 * n; ++k) b->vel[k] += hm * b->force[k];
-    if (p->flow_mode == ORC_FLOW_AFBC) {
+    if (p->flow_mode == ORC_FLOW_AFBC && p->afbc_mode == 1) {
+      /* R8 alternative: BC beads keep their velocity about the mean of the BC
+       * beads of their cell (cells of the engine's FP32 width E/n_c). */
+      int nc[3];
+      double wf[3];
+      for (int a = 0; a < 3; ++a) {
+        nc[a] = (a == 2 && p->dim == 2) ? 1 : (int)floor(b->edge[a] / p->rc);
+        wf[a] = (double)((float)b->edge[a] / (float)nc[a]);
+      }
+      const int ncell = nc[0] * nc[1] * nc[2];
+      double* sum = (double*)calloc((size_t)ncell * 4, sizeof(double));
+      int* cell = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+      for (int i = 0; i < n; ++i) {
+        int ci[3];
+        for (int a = 0; a < 3; ++a) {
+          ci[a] = (int)floor(b->pos[3 * i + a] / wf[a]);
+          if (ci[a] < 0) ci[a] = 0;
+          if (ci[a] >= nc[a]) ci[a] = nc[a] - 1;
+        }
+        cell[i] = ci[0] + nc[0] * (ci[1] + nc[1] * ci[2]);
+        if (orc_afbc_region(p, b->edge, &b->pos[3 * i]) != 1) continue;
+        for (int a = 0; a < 3; ++a) sum[4 * cell[i] + a] += b->vel[3 * i + a];
+        sum[4 * cell[i] + 3] += 1.0;
+      }
+      for (int i = 0; i < n; ++i) {
+        if (orc_afbc_region(p, b->edge, &b->pos[3 * i]) != 1) continue;
+        double u[3];
+        streaming_velocity(p, b, L, i, u);
+        const double* m = &sum[4 * cell[i]];
+        for (int a = 0; a < 3; ++a) b->vel[3 * i + a] = u[a] + (b->vel[3 * i + a] - m[a] / m[3]);
+      }
+      free(sum);
+      free(cell);
+    } else if (p->flow_mode == ORC_FLOW_AFBC) {
       for (int i = 0; i < n; ++i) {
         if (orc_afbc_region(p, b->edge, &b->pos[3 * i]) != 1) continue;
         double u[3];

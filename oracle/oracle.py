@@ -29,7 +29,7 @@ class DpdParams(C.Structure):
         ("seed", C.c_uint64), ("flow_mode", C.c_int),
         ("core_frac", C.c_double), ("bc_frac", C.c_double),
         ("dpd_on_bonded", C.c_int), ("alpha", C.c_double), ("lambda_star", C.c_double),
-        ("dim", C.c_int), ("exclude_bonds", C.c_int),
+        ("dim", C.c_int), ("exclude_bonds", C.c_int), ("afbc_mode", C.c_int),
     ]
 
 
@@ -133,7 +133,7 @@ def dpd_params(**kw):
     defaults = dict(a_ij=25.0, gamma=4.5, sigma=3.0, kBT=1.0, rc=1.0, H_fene=30.0, R0=1.5,
                     dt=0.01, mass=1.0, seed=1, flow_mode=FLOW_PERIODIC,
                     core_frac=24.0 / 76.0, bc_frac=13.0 / 76.0, dpd_on_bonded=1,
-                    alpha=1.0, lambda_star=1.0, dim=3, exclude_bonds=0)
+                    alpha=1.0, lambda_star=1.0, dim=3, exclude_bonds=0, afbc_mode=0)
     defaults.update(kw)
     return DpdParams(**defaults)
 

@@ -278,3 +278,44 @@ def test_bond_exclusion_stops_at_chain_ends():
                         exclude_bonds=3)
     f3, _, _ = O.compute_forces(par3, b)
     assert np.array_equal(f3, f)
+
+
+@pytest.mark.parametrize("dim", [3, 2])
+def test_afbc_peculiar_mode_keeps_shell_thermal_and_imposes_cell_means(dim):
+    # afbc_mode = 1 (R8's alternative): every BC bead gets v = L r' + (v -
+    # mean of the BC beads of its cell): per cell the BC beads' mean velocity
+    # relative to the imposed field is zero, their spread about it is thermal;
+    # positions and the other beads' velocities match afbc_mode = 0
+    L = np.array([0.2, 0.5, 0.0, 0.0, -0.2, 0.0, 0.0, 0.0, 0.0])
+    E = 9.0
+    if dim == 3:
+        edge, n = (E, E, E), int(round(3 * E ** 3))
+    else:
+        edge, n = (E, E, 1.0), int(round(4 * E * E))
+    p0, v0 = S.initial_box_state(edge, n, 3, 0, L=L, dim=dim)
+    boxes = {}
+    for mode in (0, 1):
+        par = O.dpd_params(flow_mode=O.FLOW_AFBC, afbc_mode=mode, dim=dim)
+        b = O.Box(edge, p0, v0, n_chains=n // 20, chain_len=10)
+        O.compute_forces(par, b, L)
+        O.advance(par, b, L, 1)
+        boxes[mode] = (b, par)
+    b0, par0 = boxes[0]
+    b1, _ = boxes[1]
+    assert np.array_equal(b0.pos, b1.pos)
+    reg = np.array([O.afbc_region(par0, edge, b1.pos[i]) for i in range(n)])
+    assert np.array_equal(b0.vel[reg != 1], b1.vel[reg != 1])
+    u = (b1.pos - 0.5 * np.array(edge)) @ L.reshape(3, 3).T
+    nc = [int(np.floor(e)) for e in edge]
+    if dim == 2:
+        nc[2] = 1
+    wf = np.array([np.float32(np.float32(e) / np.float32(k)) for e, k in zip(edge, nc)], np.float64)
+    ci = np.minimum(np.floor(b1.pos / wf).astype(int), np.array(nc) - 1)
+    cell = ci[:, 0] + nc[0] * (ci[:, 1] + nc[1] * ci[:, 2])
+    d = (b1.vel - u)[reg == 1]
+    cb = cell[reg == 1]
+    for c in np.unique(cb):
+        assert np.abs(d[cb == c].mean(axis=0)).max() < 1e-12
+    moving = 3 if dim == 3 else 2
+    assert d[:, :moving].var() > 0.3  # thermal, not frozen
+    assert np.abs((b0.vel - u)[reg == 1]).max() < 1e-12  # mode 0: exact overwrite
