@@ -87,6 +87,11 @@ typedef struct {
                            at most K bonds apart (LAMMPS special_bonds lj 0 0 0 is K = 3);
                            dpd_on_bonded = 0 means K >= 1.  FENE bonds are unaffected.
                            Other values return LHMM_ERR_ARG. */
+  int afbc_mode;        /* 0: every BC-shell bead takes v = lambda* L r' after the second
+                           half kick (Eq. micro_bc, full overwrite); 1: it keeps its
+                           velocity about the mean of the BC beads of its cell,
+                           v = lambda* L r' + (v - mean_cell(v)), so the shell stays
+                           thermal.  Other values return LHMM_ERR_ARG. */
 } lhmm_dpd_params;
 
 /* A batch of independent boxes.  Box b has edges box_edge[3b..3b+2] (its

@@ -76,6 +76,7 @@ struct MicroArgs {
   int flow, dpd_on_bonded, chain_len;
   int n_rows;                // rows of the upper half-stencil: 5 in 3D, 2 in 2D
   int excl;                  // DPD pairs of one chain up to excl bonds apart are skipped
+  int afbc_peculiar;         // BC beads keep their velocity about their cell's BC mean
   int max_beads, max_cells;
   int n_boxes;
   int* work_counter;         // persistent mode: next work item (NULL: one block per item)
@@ -153,6 +154,51 @@ __device__ __forceinline__ void cell_coords(int c, int nx, int nxy, float inx, f
   const int rem = c - cz * nxy;
   cy = __float2int_rd((static_cast<float>(rem) + 0.5f) * inx);
   cx = rem - cy * nx;
+}
+
+// R8's alternative AFBC: per cell, the BC beads keep their velocity about
+// the mean velocity of the cell's BC beads, around the imposed field L r'.
+// Kept out of line: it runs only in that mode, and inlined it would take
+// registers from the pair loop of every mode.
+__device__ __noinline__ void afbc_peculiar_pass(float* ox, int NM, const unsigned short* perm,
+                                                const unsigned short* cstart, const BoxInfo* B,
+                                                const float* sL, int C, int nx, int nxy,
+                                                float inx, float inxy) {
+  float *oy = ox + NM, *oz = oy + NM, *vx = oz + NM, *vy = vx + NM, *vz = vy + NM;
+  const float wx = B->w[0], wy = B->w[1], wz = B->w[2];
+  const float hx = 0.5f * B->len[0], hy = 0.5f * B->len[1], hz = 0.5f * B->len[2];
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    int cx, cy, cz;
+    cell_coords(c, nx, nxy, inx, inxy, cx, cy, cz);
+    const int q0 = cstart[c], q1 = cstart[c + 1];
+    float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+    int nb = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int q = q0; q < q1; ++q) {
+        const int i = perm[q];
+        const float rpx = static_cast<float>(cx) * wx + ox[i] - hx;
+        const float rpy = static_cast<float>(cy) * wy + oy[i] - hy;
+        const float rpz = static_cast<float>(cz) * wz + oz[i] - hz;
+        const bool core = fabsf(rpx) < B->half_core[0] && fabsf(rpy) < B->half_core[1] &&
+                          fabsf(rpz) < B->half_core[2];
+        const bool inbc = fabsf(rpx) < B->half_bc[0] && fabsf(rpy) < B->half_bc[1] &&
+                          fabsf(rpz) < B->half_bc[2];
+        if (core || !inbc) continue;
+        if (pass == 0) {
+          m0 += vx[i]; m1 += vy[i]; m2 += vz[i];
+          ++nb;
+        } else {
+          vx[i] = sL[0] * rpx + sL[1] * rpy + sL[2] * rpz + (vx[i] - m0);
+          vy[i] = sL[3] * rpx + sL[4] * rpy + sL[5] * rpz + (vy[i] - m1);
+          vz[i] = sL[6] * rpx + sL[7] * rpy + sL[8] * rpz + (vz[i] - m2);
+        }
+      }
+      if (pass == 0 && nb > 0) {
+        const float inv = 1.f / static_cast<float>(nb);
+        m0 *= inv; m1 *= inv; m2 *= inv;
+      }
+    }
+  }
 }
 
 template <int T>
@@ -542,7 +588,11 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
           int m0 = 0;
           if (row != 0) {
             const float w2s = has_window ? w2 : 1e-12f;
-            const float w = w2s * rsqrtf(w2s) + 1e-5f;  // margin covers rsqrtf's error
+            // margin covers rsqrtf's error; capped at the cell width (every
+            // true pair has |dx| < rc <= wx), so a window of 2w never reaches
+            // a fourth cell, which the two cell-start slots e0, e1 below
+            // could not place
+            const float w = fminf(w2s * rsqrtf(w2s) + 1e-5f, wx);
             float cc = xa - sxr;  // in (-lenx, 2 lenx)
             const bool neg = cc < 0.f, big = cc >= lenx;
             cc = neg ? cc + lenx : (big ? cc - lenx : cc);
@@ -698,7 +748,7 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
         u0 = sL[0] * rpx + sL[1] * rpy + sL[2] * rpz;
         u1 = sL[3] * rpx + sL[4] * rpy + sL[5] * rpz;
         u2 = sL[6] * rpx + sL[7] * rpy + sL[8] * rpz;
-        if (!core && inbc) {
+        if (!core && inbc && !A.afbc_peculiar) {
           v0 = u0; v1 = u1; v2 = u2;
         }
         sample = core;
@@ -715,6 +765,10 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
         W[4] += A.mass * d0 * d2;
         W[5] += A.mass * d1 * d2;
       }
+    }
+    if (afbc && A.afbc_peculiar) {
+      __syncthreads();
+      afbc_peculiar_pass(ox, NM, perm, cstart, &sB, sL, C, nx, nxy, inx, inxy);
     }
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
@@ -959,6 +1013,7 @@ MicroArgs make_args(const lhmm_micro_s* h) {
   a.dpd_on_bonded = p.dpd_on_bonded;
   a.n_rows = p.dim == 2 ? 2 : 5;
   a.excl = std::max(p.exclude_bonds, p.dpd_on_bonded ? 0 : 1);
+  a.afbc_peculiar = p.afbc_mode == 1;
   a.chain_len = h->chain_len > 0 ? h->chain_len : 1;
   a.max_beads = h->max_beads;
   a.max_cells = h->max_cells;
@@ -1004,7 +1059,8 @@ extern "C" lhmm_status lhmm_micro_create(const lhmm_dpd_params* params,
   const lhmm_dpd_params& p = *params;
   if (!(p.rc > 0.f) || !(p.dt > 0.f) || !(p.mass > 0.f) || !(p.R0 > 0.f) ||
       !(p.lambda_star != 0.0) || p.flow_mode < 0 || p.flow_mode > 2 ||
-      (p.dim != 0 && p.dim != 2 && p.dim != 3) || p.exclude_bonds < 0 || p.exclude_bonds > 3)
+      (p.dim != 0 && p.dim != 2 && p.dim != 3) || p.exclude_bonds < 0 || p.exclude_bonds > 3 ||
+      (p.afbc_mode != 0 && p.afbc_mode != 1))
     return LHMM_ERR_ARG;
   const bool planar = p.dim == 2;
   const int nb = batch->n_boxes;

@@ -33,7 +33,7 @@ class DpdParams(C.Structure):
         ("mass", C.c_float), ("seed", C.c_uint64), ("flow_mode", C.c_int),
         ("afbc_core_frac", C.c_float), ("afbc_bc_frac", C.c_float), ("dpd_on_bonded", C.c_int),
         ("alpha", C.c_double), ("lambda_star", C.c_double), ("dim", C.c_int),
-        ("exclude_bonds", C.c_int),
+        ("exclude_bonds", C.c_int), ("afbc_mode", C.c_int),
     ]
 
 
@@ -158,14 +158,15 @@ def _np(a, dtype):
 
 def dpd_params(flow="afbc", seed=1, alpha=1.0, lambda_star=1.0, dpd_on_bonded=1,
                afbc_core_frac=24.0 / 76.0, afbc_bc_frac=13.0 / 76.0, dim=3, exclude_bonds=0,
-               **phys):
+               afbc_mode=0, **phys):
     d = dict(a_ij=25.0, gamma=4.5, sigma=3.0, kBT=1.0, rc=1.0, H_fene=30.0, R0=1.5, dt=0.01,
              mass=1.0)
     d.update(phys)
     flow_mode = FLOWS[flow] if isinstance(flow, str) else int(flow)
     return DpdParams(seed=seed, flow_mode=flow_mode, afbc_core_frac=afbc_core_frac,
                      afbc_bc_frac=afbc_bc_frac, dpd_on_bonded=dpd_on_bonded, alpha=alpha,
-                     lambda_star=lambda_star, dim=dim, exclude_bonds=exclude_bonds, **d)
+                     lambda_star=lambda_star, dim=dim, exclude_bonds=exclude_bonds,
+                     afbc_mode=afbc_mode, **d)
 
 
 class Micro:

@@ -121,7 +121,7 @@ def stress_relaxation(chain_len, shear_rate, replicas=64, edge=20.0, shear_time=
 
 def planar_extension(chain_len, rates, replicas=32, edge=36.0, equil_time=None,
                      sample_time=None, call_steps=1000, seed=17, exclude_bonds=0,
-                     mode="extension"):
+                     mode="extension", afbc_mode=0):
     """Steady planar extension L = diag(e, -e) imposed through the AFBC shell
     of 2D melt boxes; planar extensional viscosity eta_P = (pi_xx - pi_yy)/e
     from the core's IK stress.  For a Newtonian liquid eta_P = 4 eta (the
@@ -148,7 +148,7 @@ def planar_extension(chain_len, rates, replicas=32, edge=36.0, equil_time=None,
     batch = synth.make_batch(np.full(B, edge), L, seed, flow="afbc", chain_len=chain_len,
                              fraction=1.0, n_beads=np.full(B, n), dim=2)
     params = lhmm.dpd_params(flow="afbc", seed=seed, dim=2, exclude_bonds=exclude_bonds,
-                             **PAPER_2D)
+                             afbc_mode=afbc_mode, **PAPER_2D)
     t0 = time.perf_counter()
     m = lhmm.Micro.from_batch(params, batch)
     Ld = torch.from_numpy(L).cuda()
@@ -169,6 +169,7 @@ def planar_extension(chain_len, rates, replicas=32, edge=36.0, equil_time=None,
         etaP = (mean[:, :, 0] - mean[:, :, 1]) / rates[:, None]
     m.close()
     return dict(chain_len=chain_len, rates=rates.tolist(), replicas=replicas, edge=edge,
-                mode=mode, beads_per_box=n, eta_P=etaP.mean(axis=1).tolist(),
+                mode=mode, afbc_mode=afbc_mode, beads_per_box=n,
+                eta_P=etaP.mean(axis=1).tolist(),
                 eta_P_se=(etaP.std(axis=1, ddof=1) / np.sqrt(replicas)).tolist(),
                 wall_s=time.perf_counter() - t0, device_status=status)

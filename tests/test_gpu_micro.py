@@ -248,6 +248,28 @@ def test_bond_overstretch_reported_without_fault():
     m.close()
 
 
+def test_strong_extension_overstretches_on_both_sides():
+    # planar extension through the overwritten BC shell pulls chains apart:
+    # at rate 3 both the kernel and the oracle flag an over-stretched bond
+    # within 100 steps, while the same boxes under rate-0.01 extension do not
+    lh = _lh()
+    edges = np.array([8.0, 9.0])
+    for rate, expect in ((3.0, True), (0.01, False)):
+        L = np.zeros((2, 9), np.float32)
+        L[:, 0], L[:, 4] = rate, -rate
+        batch = S.make_batch(edges, L, 31, flow="afbc")
+        m, op, boxes = _pair(batch, "afbc", seed=31)
+        st = torch.zeros((2, 6), dtype=torch.float64, device="cuda")
+        m.advance(torch.from_numpy(batch.L).cuda(), 100, st)
+        _, per_box = m.sync(raise_on_error=False)
+        for b, ob in enumerate(boxes):
+            _, _, err = O.advance(op, ob, batch.L[b], 100)
+            gpu_flag = bool(per_box[b] & lh.BOX_BOND_OVERSTRETCH)
+            orc_flag = bool(err & O.ERR_BOND_OVERSTRETCH)
+            assert gpu_flag == orc_flag == expect, (rate, b, gpu_flag, orc_flag)
+        m.close()
+
+
 def test_host_buffer_entry_point_matches_device_one():
     batch = _ragged_afbc_batch(seed=6)
     lh = _lh()
@@ -340,4 +362,22 @@ def test_bonded_pairs_excluded_matches_oracle():
     for b, ob in enumerate(boxes):
         _, _, f, _, _ = m.get_state(b)
         assert np.abs(f - ob.force).max() <= 1e-4, (b, np.abs(f - ob.force).max())
+    m.close()
+
+
+def test_afbc_peculiar_mode_matches_oracle():
+    # afbc_mode = 1: BC beads keep their velocity about their cell's BC mean;
+    # a 50-step trajectory and, restarted from the GPU state, each step's update
+    from afbc_steps import stepwise_afbc_parity
+    batch = _ragged_afbc_batch(seed=21)
+    m, op, boxes = _pair(batch, "afbc", seed=21, afbc_mode=1)
+    L = torch.from_numpy(batch.L).cuda()
+    st = torch.zeros((batch.n_boxes, 6), dtype=torch.float64, device="cuda")
+    m.advance(L, 1, st)
+    m.sync()
+    for b, ob in enumerate(boxes):
+        O.advance(op, ob, batch.L[b], 1)
+        _, vel, _, _, _ = m.get_state(b)
+        assert np.abs(vel - ob.vel).max() <= 1e-4, (b, np.abs(vel - ob.vel).max())
+    assert stepwise_afbc_parity(m, op, batch, 30) <= 10
     m.close()

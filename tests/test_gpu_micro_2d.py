@@ -150,3 +150,21 @@ def test_2d_bond_exclusion_matches_oracle(K):
         pos, _, _, _, _ = m.get_state(b)
         assert np.abs(_minimage(pos - ob.pos, batch.edges[b][0])).max() <= 1e-3
     m.close()
+
+
+def test_2d_afbc_peculiar_mode_matches_oracle():
+    # R8's alternative on the GPU: each step's AFBC update (BC beads keep
+    # their velocity about their cell's BC mean) against the oracle, restarted
+    # from the GPU state before every step
+    from afbc_steps import stepwise_afbc_parity
+    from paper_2512_13267_gb300 import lhmm as lh
+    batch = _batch("afbc", 23)
+    gp = lh.dpd_params(flow="afbc", seed=23, dim=2, afbc_mode=1, **PAPER)
+    op = O.dpd_params(flow_mode=O.FLOW_AFBC, seed=23, dim=2, afbc_mode=1, **PAPER)
+    m = lh.Micro.from_batch(gp, batch)
+    skipped = stepwise_afbc_parity(m, op, batch, 50, dim=2)
+    assert skipped <= 10
+    for b in range(batch.n_boxes):
+        _, vel, _, _, _ = m.get_state(b)
+        assert np.all(vel[:, 2] == 0.0)
+    m.close()
