@@ -201,7 +201,7 @@ __device__ __noinline__ void afbc_peculiar_pass(float* ox, int NM, const unsigne
   }
 }
 
-template <int T>
+template <int T, bool PEC>
 __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ BoxInfo sB;
@@ -514,15 +514,16 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
         // x_i + rc], (0,+1), (+1,-1), (+1,0), (+1,+1) [an x window each]
         const int dz = row < 2 ? 0 : 1;
         const int dy = row == 0 ? 0 : (row == 1 ? 1 : row - 3);
-        // up to two slot ranges (two when the window wraps around the row);
-        // per range the first slot, the length, the slots e0, e1 where its
-        // 2nd and 3rd x cells start, and xb = x_i - dc*wx - shift with dc the
-        // x cell offset of its first cell (j's image relative to i), so that
-        // for slot q rx = xb - wx*[(q >= e0) + (q >= e1)] - ox[j]
-        int s1 = 0, len1 = 0, e01 = 0, e11 = 0;
-        int s2 = 0, len2 = 0, e02 = 0, e12 = 0;
-        float xb1 = 0.f, xb2 = 0.f;
-        unsigned hw1 = 0u, hw2 = 0u;  // upper word of the range's queue entries at dc
+        // The window is one run of slots in unwrapped row order: candidate t
+        // (0 <= t < len) is slot s + t, or s + t - (row length) from t = tj on
+        // when the window wraps around the row end.  The run covers at most
+        // three x cells (unwrapped: c0, c0 + 1, c0 + 2, starting at t = 0,
+        // t0, t1); xb = x_i - dc*wx - shift with dc the x cell offset of c0
+        // (j's image relative to i), so rx = xb - wx*[(t >= t0) + (t >= t1)]
+        // - ox[j], and hw is the upper word of a queue entry in cell c0.
+        int s = 0, sw = 0, tj = 0x7fffffff, len = 0, t0 = 0, t1 = 0;
+        float xb0 = 0.f, xb1 = 0.f, xb2 = 0.f;
+        unsigned hw0 = 0u;
         const int z = wrapi(cz + dz, nz);
         int y = cy + dy;
         const bool below = y < 0, above = y >= ny;
@@ -571,17 +572,6 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
             cell = c;
             return lo;
           };
-          // the range from slot q0 (in x cell ca, image m of the row) to q1
-          auto set_range = [&](int q0, int q1, int ca, int m, int& sr, int& lr, int& e0r,
-                               int& e1r, float& xbr, unsigned& hwr) {
-            const int dc = ca + m * nx - cx;
-            sr = q0;
-            lr = max(q1 - q0, 0);
-            e0r = cstart[rowbase + ca + 1];
-            e1r = ca + 2 <= nx ? cstart[rowbase + ca + 2] : 0x7fffffff;
-            xbr = (-static_cast<float>(dc) * wx - sxr) + xi;
-            hwr = hiw + static_cast<unsigned>(dc + kDcxBias);
-          };
           // window [X0, X1) in unwrapped row coordinates (image m0); the own
           // row starts right after slot k
           float X0 = xa, X1 = xa + A.rc + 1e-5f;
@@ -605,17 +595,24 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
           const int q0 = (row == 0) ? k + 1 : lower(wl ? X0 + lenx : X0, c0);
           const int q1 = lower(wh ? X1 - lenx : X1, c1);
           const int rowstart = cstart[rowbase], rowend = cstart[rowbase + nx];
-          set_range(q0, wrap ? rowend : q1, c0, wl ? m0 - 1 : m0, s1, len1, e01, e11, xb1, hw1);
-          set_range(rowstart, wrap ? q1 : rowstart, 0, wl ? m0 : m0 + 1, s2, len2, e02, e12,
-                    xb2, hw2);
-          len1 = has_window ? len1 : 0;
-          len2 = has_window ? len2 : 0;
+          const int dc = c0 + (wl ? m0 - 1 : m0) * nx - cx;
+          s = q0;
+          sw = q0 - (rowend - rowstart);
+          tj = wrap ? rowend - q0 : 0x7fffffff;
+          len = wrap ? (rowend - q0) + (q1 - rowstart) : max(q1 - q0, 0);
+          len = has_window ? len : 0;
+          // slot offsets of the next two cells (past the row end: the row's
+          // first cells, one image on)
+          t0 = cstart[rowbase + c0 + 1] - q0;
+          t1 = (c0 + 2 <= nx ? cstart[rowbase + c0 + 2] : rowend + cstart[rowbase + 1] - rowstart) - q0;
+          xb0 = (-static_cast<float>(dc) * wx - sxr) + xi;
+          xb1 = xb0 - wx;
+          xb2 = xb1 - wx;
+          hw0 = hiw + static_cast<unsigned>(dc + kDcxBias);
         }
-        const int len = len1 + len2;
         const int lmax = __reduce_max_sync(FULL, len);
         const float yb = -static_cast<float>(dy) * wy + yi, zb = -static_cast<float>(dz) * wz + zi;
         const unsigned lo_i = static_cast<unsigned>(i);
-        const int s2o = s2 - len1;
         // fill the warp's queue from the slot windows; whenever it holds 32
         // pairs, leave the (register-light) fill loop to evaluate them
         int t = 0;
@@ -625,12 +622,10 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
             unsigned lo_w, hi_w;
             {  // no divergent branch: lanes past their window test slot 0
               const bool act = t < len;
-              const bool first = t < len1;
-              const int q = act ? t + (first ? s1 : s2o) : 0;
-              const bool p0 = q >= (first ? e01 : e02), p1 = q >= (first ? e11 : e12);
-              float bx = first ? xb1 : xb2;
-              bx = p0 ? bx - wx : bx;
-              bx = p1 ? bx - wx : bx;
+              const bool p0 = t >= t0, p1 = t >= t1;
+              int q = t + (t >= tj ? sw : s);
+              q = act ? q : 0;
+              const float bx = p1 ? xb2 : (p0 ? xb1 : xb0);
               const int j = perm[q];
               const float rx = bx - ox[j];
               const float ry = yb - oy[j];
@@ -642,7 +637,7 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
                 hit = hit && !(d <= A.excl && lo + d < sB.n_poly && (lo % A.chain_len) + d < A.chain_len);
               }
               lo_w = lo_i | (static_cast<unsigned>(j) << 16);
-              hi_w = (first ? hw1 : hw2) + static_cast<unsigned>(p0) + static_cast<unsigned>(p1);
+              hi_w = hw0 + static_cast<unsigned>(p0) + static_cast<unsigned>(p1);
             }
             const unsigned bal = __ballot_sync(FULL, hit);
             // every lane stores (no divergent branch): misses go to the spare
@@ -748,7 +743,7 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
         u0 = sL[0] * rpx + sL[1] * rpy + sL[2] * rpz;
         u1 = sL[3] * rpx + sL[4] * rpy + sL[5] * rpz;
         u2 = sL[6] * rpx + sL[7] * rpy + sL[8] * rpz;
-        if (!core && inbc && !A.afbc_peculiar) {
+        if (!core && inbc && !PEC) {
           v0 = u0; v1 = u1; v2 = u2;
         }
         sample = core;
@@ -766,7 +761,7 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
         W[5] += A.mass * d1 * d2;
       }
     }
-    if (afbc && A.afbc_peculiar) {
+    if (PEC && afbc) {
       __syncthreads();
       afbc_peculiar_pass(ox, NM, perm, cstart, &sB, sL, C, nx, nxy, inx, inxy);
     }
@@ -817,16 +812,18 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
 }
 
 
-// One block per listed box.
-template <int T, int MINB>
+// One block per listed box.  PEC: the AFBC shell keeps the beads' peculiar
+// velocity (a separate instantiation, so the other modes' register
+// allocation does not carry that pass).
+template <int T, int MINB, bool PEC>
 __global__ void __launch_bounds__(T, MINB) micro_kernel(const MicroArgs A) {
-  micro_box<T>(A, A.list[blockIdx.x]);
+  micro_box<T, PEC>(A, A.list[blockIdx.x]);
 }
 
 // Persistent form: a fixed grid whose blocks pull item indices from a device
 // counter up to a device-side count, so the set of boxes can be chosen on the
 // device (e.g. by a gate inside a CUDA graph).
-template <int T, int MINB>
+template <int T, int MINB, bool PEC>
 __global__ void __launch_bounds__(T, MINB) micro_kernel_persistent(const MicroArgs A) {
   __shared__ int s_item;
   const int limit = min(*A.n_items_dev, A.max_items);
@@ -836,7 +833,7 @@ __global__ void __launch_bounds__(T, MINB) micro_kernel_persistent(const MicroAr
     const int item = s_item;
     __syncthreads();
     if (item >= limit) return;
-    micro_box<T>(A, A.list[item]);
+    micro_box<T, PEC>(A, A.list[item]);
     __syncthreads();
   }
 }
@@ -849,25 +846,31 @@ struct Variant {
 constexpr Variant kVariants[] = {{256, 4}, {512, 2}, {1024, 1}, {256, 2}, {512, 1}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
-template <int T, int MINB>
-cudaError_t launch_micro(const MicroArgs& a, int grid, size_t smem, cudaStream_t s) {
+template <int T, int MINB, bool PEC>
+cudaError_t launch_micro_mode(const MicroArgs& a, int grid, size_t smem, cudaStream_t s) {
   static size_t attr_bytes = 0, attr_bytes_p = 0;
   const bool persistent = a.work_counter != nullptr;
   size_t& done = persistent ? attr_bytes_p : attr_bytes;
   if (smem > done) {
     cudaError_t e = persistent
-                        ? cudaFuncSetAttribute(micro_kernel_persistent<T, MINB>,
+                        ? cudaFuncSetAttribute(micro_kernel_persistent<T, MINB, PEC>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                static_cast<int>(smem))
-                        : cudaFuncSetAttribute(micro_kernel<T, MINB>,
+                        : cudaFuncSetAttribute(micro_kernel<T, MINB, PEC>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     done = smem;
   }
-  if (persistent) micro_kernel_persistent<T, MINB><<<grid, T, smem, s>>>(a);
-  else micro_kernel<T, MINB><<<grid, T, smem, s>>>(a);
+  if (persistent) micro_kernel_persistent<T, MINB, PEC><<<grid, T, smem, s>>>(a);
+  else micro_kernel<T, MINB, PEC><<<grid, T, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int T, int MINB>
+cudaError_t launch_micro(const MicroArgs& a, int grid, size_t smem, cudaStream_t s) {
+  return a.afbc_peculiar ? launch_micro_mode<T, MINB, true>(a, grid, smem, s)
+                         : launch_micro_mode<T, MINB, false>(a, grid, smem, s);
 }
 
 cudaError_t launch_variant(int v, const MicroArgs& a, int grid, size_t smem, cudaStream_t s) {
