@@ -40,10 +40,10 @@ ALGO_OPS_PER_BEAD_STEP = PAIRS_PER_BEAD * OPS_PER_PAIR + OPS_PER_BEAD
 N_SM = 152
 LANES_PER_SM_CLK = 128
 # DRAM bytes (read + write) per bead and call of micro_kernel, from the ncu
-# capture in profiles/micro_kernel_e12_304box_full.md (75.79 + 15.93 MB for
+# capture in profiles/micro_kernel_e12_304box_full.md (75.76 + 15.11 MB for
 # 1,575,936 beads); the kernel reads and writes box state once per call, so
 # traffic scales with beads, not with DPD steps.
-DRAM_BYTES_PER_BEAD_CALL = 91.718e6 / 1575936
+DRAM_BYTES_PER_BEAD_CALL = 90.873e6 / 1575936
 
 
 def _peaks():
@@ -116,7 +116,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_rate(batch, budget_s=12.0, min_s=6.0, chunk_steps=5, n_boxes=24):
+def cpu_oracle_rate(batch, budget_s=20.0, min_s=10.0, chunk_steps=5, n_boxes=24):
     """FP64 oracle (OpenMP over boxes) on a fixed sample of the same workload.
     Returns (bead-steps/s, threads, description)."""
     sys.path.insert(0, os.path.join(ROOT, "oracle"))
