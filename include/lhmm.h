@@ -186,8 +186,16 @@ lhmm_status lhmm_micro_info(lhmm_micro_t h, int* n_boxes, int64_t* total_beads, 
  * stream), with a shared-memory plan sized to its largest box and one of
  * LHMM_MICRO_N_VARIANTS kernel variants (threads per block x resident blocks
  * per SM).  A subset advance (box_idx_dev != NULL) is one launch sized to the
- * largest box of the batch. */
-#define LHMM_MICRO_N_VARIANTS 5
+ * largest box of the batch.
+ * Variants 0..4 hold a box in one SM's shared memory (up to about 5 700
+ * beads in 3D).  Variants 5 (512 threads) and 6 (256 threads x 2 blocks) hold
+ * it in a per-box scratch buffer in device memory, served by L1/L2, for boxes
+ * beyond that (up to 65 535 beads and 65 535 cells; the paper's 76 x 76 melt
+ * box has 23 104); the handle allocates that buffer (n_boxes x the largest
+ * box's plan) when a class needs it or a class is pinned to such a variant.
+ * Both kinds run the same arithmetic in the same order, so they give
+ * bit-identical results. */
+#define LHMM_MICRO_N_VARIANTS 7
 
 /* Time every variant on probe_steps steps of each class's boxes under L_dev
  * (device, n_boxes x 9) and keep the fastest per class; results are cached
@@ -204,7 +212,9 @@ lhmm_status lhmm_micro_plan(lhmm_micro_t h, int* n_classes, int cap, int* class_
                             int* class_max_beads, int* class_threads, int* class_min_blocks);
 
 /* Pin the kernel variant (0..LHMM_MICRO_N_VARIANTS-1) of one class.  Returns
- * LHMM_ERR_UNSUPPORTED if that variant's shared-memory plan does not fit. */
+ * LHMM_ERR_UNSUPPORTED if that variant's shared-memory plan does not fit.
+ * Pinning a device-memory variant (5, 6) may allocate the scratch buffer:
+ * call it before capturing advances into a CUDA graph. */
 lhmm_status lhmm_micro_set_variant(lhmm_micro_t h, int cls, int variant);
 
 /* ------------------------------------------------------------------------

@@ -82,6 +82,8 @@ struct MicroArgs {
   int* work_counter;         // persistent mode: next work item (NULL: one block per item)
   const int* n_items_dev;    // persistent mode: device-side item count
   int max_items;             // persistent mode: capacity of the item list
+  unsigned char* gm;         // boxes held in global memory: per-box scratch (else NULL)
+  size_t gm_stride;          // bytes of scratch per box
 };
 
 constexpr int kRedFloats = 192;  // 6 x 32 warps, also scan scratch
@@ -94,19 +96,30 @@ constexpr int kQueue = 65;       // pair-queue entries per warp (64 + a slot for
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
-// Shared-memory plan of a box of up to N beads and C cells, T threads.
-__host__ __device__ inline size_t micro_smem_bytes(int N, int C, int T) {
+// Memory plan of a box of up to N beads and C cells: the box arrays ...
+__host__ __device__ inline size_t micro_box_bytes(int N, int C) {
   size_t b = 9 * sizeof(float) * (size_t)N;    // offsets, velocities, forces (SoA)
   b += 2 * sizeof(unsigned short) * (size_t)N;  // cell id per bead, sorted slot -> bead
   b = align16(b);
   b += sizeof(unsigned short) * (size_t)(C + 1); // cell start offsets
   b = align16(b);
   b += sizeof(unsigned short) * (size_t)(C + 1); // cell counters (packed in 32-bit words)
-  b = align16(b);
-  b += sizeof(unsigned long long) * (size_t)kQueue * (T / 32);  // pair queues
+  return align16(b);
+}
+
+// ... and the per-block buffers of T threads, always in shared memory.
+__host__ __device__ inline size_t micro_block_bytes(int T) {
+  size_t b = sizeof(unsigned long long) * (size_t)kQueue * (T / 32);  // pair queues
   b += sizeof(float) * kRedFloats;
   b += sizeof(double) * 12;  // FP64 stress sums
   return b;
+}
+
+// Shared memory of one block: box arrays and block buffers (GM: a box held
+// in global memory, whose arrays live in a per-box scratch buffer in HBM and
+// are served by L1/L2; for boxes beyond one SM's shared memory).
+__host__ __device__ inline size_t micro_smem_bytes(int N, int C, int T, bool gm = false) {
+  return (gm ? 0 : micro_box_bytes(N, C)) + micro_block_bytes(T);
 }
 
 __device__ __forceinline__ int wrapi(int c, int n) {
@@ -201,7 +214,7 @@ __device__ __noinline__ void afbc_peculiar_pass(float* ox, int NM, const unsigne
   }
 }
 
-template <int T, bool PEC>
+template <int T, bool PEC, bool GM>
 __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ BoxInfo sB;
@@ -218,10 +231,12 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
   const float inx = 1.f / static_cast<float>(nx), inxy = 1.f / static_cast<float>(nxy);
   const float wx = sB.w[0], wy = sB.w[1], wz = sB.w[2];
 
-  // carve shared memory (same plan as micro_smem_bytes)
+  // carve the box arrays (shared memory, or the box's global scratch) and
+  // the block buffers (same plan as micro_smem_bytes)
   const int NM = A.max_beads, CM = A.max_cells;
+  unsigned char* const boxmem = GM ? A.gm + static_cast<size_t>(bid) * A.gm_stride : smem;
   BoxView S;
-  S.ox = reinterpret_cast<float*>(smem);
+  S.ox = reinterpret_cast<float*>(boxmem);
   S.oy = S.ox + NM;
   S.oz = S.oy + NM;
   S.vx = S.oz + NM;
@@ -233,11 +248,12 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
   S.cellid = reinterpret_cast<unsigned short*>(S.fz + NM);
   S.perm = S.cellid + NM;
   size_t b = align16(9 * sizeof(float) * (size_t)NM + 2 * sizeof(unsigned short) * (size_t)NM);
-  S.cstart = reinterpret_cast<unsigned short*>(smem + b);
+  S.cstart = reinterpret_cast<unsigned short*>(boxmem + b);
   b = align16(b + sizeof(unsigned short) * (size_t)(CM + 1));
-  unsigned* cnt32 = reinterpret_cast<unsigned*>(smem + b);  // two 16-bit counters per word
+  unsigned* cnt32 = reinterpret_cast<unsigned*>(boxmem + b);  // two 16-bit counters per word
   const unsigned short* cnt16 = reinterpret_cast<const unsigned short*>(cnt32);
   b = align16(b + sizeof(unsigned short) * (size_t)(CM + 1));
+  if (GM) b = 0;  // block buffers start the shared memory
   unsigned long long* queue = reinterpret_cast<unsigned long long*>(smem + b) + kQueue * warp;
   b += sizeof(unsigned long long) * (size_t)kQueue * NW;
   float* red = reinterpret_cast<float*>(smem + b);
@@ -814,16 +830,17 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
 
 // One block per listed box.  PEC: the AFBC shell keeps the beads' peculiar
 // velocity (a separate instantiation, so the other modes' register
-// allocation does not carry that pass).
-template <int T, int MINB, bool PEC>
+// allocation does not carry that pass).  GM: the box arrays live in a
+// per-box global scratch buffer instead of shared memory.
+template <int T, int MINB, bool PEC, bool GM>
 __global__ void __launch_bounds__(T, MINB) micro_kernel(const MicroArgs A) {
-  micro_box<T, PEC>(A, A.list[blockIdx.x]);
+  micro_box<T, PEC, GM>(A, A.list[blockIdx.x]);
 }
 
 // Persistent form: a fixed grid whose blocks pull item indices from a device
 // counter up to a device-side count, so the set of boxes can be chosen on the
 // device (e.g. by a gate inside a CUDA graph).
-template <int T, int MINB, bool PEC>
+template <int T, int MINB, bool PEC, bool GM>
 __global__ void __launch_bounds__(T, MINB) micro_kernel_persistent(const MicroArgs A) {
   __shared__ int s_item;
   const int limit = min(*A.n_items_dev, A.max_items);
@@ -833,7 +850,7 @@ __global__ void __launch_bounds__(T, MINB) micro_kernel_persistent(const MicroAr
     const int item = s_item;
     __syncthreads();
     if (item >= limit) return;
-    micro_box<T, PEC>(A, A.list[item]);
+    micro_box<T, PEC, GM>(A, A.list[item]);
     __syncthreads();
   }
 }
@@ -842,45 +859,53 @@ __global__ void __launch_bounds__(T, MINB) micro_kernel_persistent(const MicroAr
 // the register allocation must allow (64 registers/thread for 2048/SM).
 struct Variant {
   int threads, min_blocks;
+  bool gm;  // box arrays in global scratch (boxes beyond one SM's shared memory)
 };
-constexpr Variant kVariants[] = {{256, 4}, {512, 2}, {1024, 1}, {256, 2}, {512, 1}};
+constexpr Variant kVariants[] = {{256, 4, false}, {512, 2, false}, {1024, 1, false},
+                                 {256, 2, false}, {512, 1, false}, {512, 1, true},
+                                 {256, 2, true}};
+constexpr int kFirstGmVariant = 5;
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+static_assert(kNumVariants == LHMM_MICRO_N_VARIANTS, "variant table and header disagree");
 
-template <int T, int MINB, bool PEC>
+template <int T, int MINB, bool PEC, bool GM>
 cudaError_t launch_micro_mode(const MicroArgs& a, int grid, size_t smem, cudaStream_t s) {
   static size_t attr_bytes = 0, attr_bytes_p = 0;
   const bool persistent = a.work_counter != nullptr;
   size_t& done = persistent ? attr_bytes_p : attr_bytes;
   if (smem > done) {
     cudaError_t e = persistent
-                        ? cudaFuncSetAttribute(micro_kernel_persistent<T, MINB, PEC>,
+                        ? cudaFuncSetAttribute(micro_kernel_persistent<T, MINB, PEC, GM>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                static_cast<int>(smem))
-                        : cudaFuncSetAttribute(micro_kernel<T, MINB, PEC>,
+                        : cudaFuncSetAttribute(micro_kernel<T, MINB, PEC, GM>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     done = smem;
   }
-  if (persistent) micro_kernel_persistent<T, MINB, PEC><<<grid, T, smem, s>>>(a);
-  else micro_kernel<T, MINB, PEC><<<grid, T, smem, s>>>(a);
+  if (persistent) micro_kernel_persistent<T, MINB, PEC, GM><<<grid, T, smem, s>>>(a);
+  else micro_kernel<T, MINB, PEC, GM><<<grid, T, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int T, int MINB>
+template <int T, int MINB, bool GM = false>
 cudaError_t launch_micro(const MicroArgs& a, int grid, size_t smem, cudaStream_t s) {
-  return a.afbc_peculiar ? launch_micro_mode<T, MINB, true>(a, grid, smem, s)
-                         : launch_micro_mode<T, MINB, false>(a, grid, smem, s);
+  return a.afbc_peculiar ? launch_micro_mode<T, MINB, true, GM>(a, grid, smem, s)
+                         : launch_micro_mode<T, MINB, false, GM>(a, grid, smem, s);
 }
 
 cudaError_t launch_variant(int v, const MicroArgs& a, int grid, size_t smem, cudaStream_t s) {
   if (grid <= 0) return cudaSuccess;
+  if (kVariants[v].gm && a.gm == nullptr) return cudaErrorInvalidValue;
   switch (v) {
     case 0: return launch_micro<256, 4>(a, grid, smem, s);
     case 1: return launch_micro<512, 2>(a, grid, smem, s);
     case 2: return launch_micro<1024, 1>(a, grid, smem, s);
     case 3: return launch_micro<256, 2>(a, grid, smem, s);
-    default: return launch_micro<512, 1>(a, grid, smem, s);
+    case 4: return launch_micro<512, 1>(a, grid, smem, s);
+    case 5: return launch_micro<512, 1, true>(a, grid, smem, s);
+    default: return launch_micro<256, 2, true>(a, grid, smem, s);
   }
 }
 
@@ -913,6 +938,8 @@ struct lhmm_micro_s {
   cudaEvent_t fork = nullptr;
   int* work_counter = nullptr;  // persistent-mode item counter
   int subset_variant = 1;  // single launch over a device-side box list
+  unsigned char* gm = nullptr;  // per-box scratch of the global-memory variants
+  size_t gm_stride = 0;
 };
 
 namespace {
@@ -925,7 +952,28 @@ size_t max_optin_smem() {
 }
 
 size_t class_smem(int max_beads, int max_cells, int variant) {
-  return micro_smem_bytes(max_beads, max_cells, kVariants[variant].threads);
+  return micro_smem_bytes(max_beads, max_cells, kVariants[variant].threads, kVariants[variant].gm);
+}
+
+// whether some shared-memory variant holds a class of this size
+bool fits_shared(int max_beads, int max_cells, size_t optin) {
+  for (int v = 0; v < kFirstGmVariant; ++v)
+    if (class_smem(max_beads, max_cells, v) <= optin) return true;
+  return false;
+}
+
+// per-box global scratch for the GM variants, sized for the largest box
+cudaError_t ensure_gm(lhmm_micro_s* h) {
+  if (h->gm) return cudaSuccess;
+  const size_t stride = micro_box_bytes(h->max_beads, h->max_cells);
+  const size_t n = static_cast<size_t>(std::max(h->n_boxes, 1));
+  cudaError_t e = cudaMalloc(&h->gm, stride * n);
+  if (e != cudaSuccess) {
+    h->gm = nullptr;
+    return e;
+  }
+  h->gm_stride = stride;
+  return cudaSuccess;
 }
 
 // heuristic start: more threads for larger boxes; the autotuner refines it
@@ -985,6 +1033,7 @@ void free_micro(lhmm_micro_t h) {
   }
   if (h->fork) cudaEventDestroy(h->fork);
   cudaFree(h->work_counter);
+  cudaFree(h->gm);
   delete h;
 }
 
@@ -1021,6 +1070,8 @@ MicroArgs make_args(const lhmm_micro_s* h) {
   a.max_beads = h->max_beads;
   a.max_cells = h->max_cells;
   a.n_boxes = h->n_boxes;
+  a.gm = h->gm;
+  a.gm_stride = h->gm_stride;
   return a;
 }
 
@@ -1110,8 +1161,8 @@ extern "C" lhmm_status lhmm_micro_create(const lhmm_dpd_params* params,
     max_cells = std::max(max_cells, B.ncell);
   }
   if (total > 0 && (!pos0_host || !vel0_host)) return LHMM_ERR_ARG;
-  // queue entries hold 16-bit bead ids; the whole box must fit in shared memory
-  if (max_beads > 8191) return LHMM_ERR_UNSUPPORTED;
+  // queue entries hold 16-bit bead ids (n <= 65535 above); a box too large
+  // for one SM's shared memory runs in a global-memory variant
   const size_t optin = max_optin_smem();
   lhmm_micro_s* h = new lhmm_micro_s();
   h->p = p;
@@ -1129,8 +1180,9 @@ extern "C" lhmm_status lhmm_micro_create(const lhmm_dpd_params* params,
   };
   if (class_smem(max_beads, max_cells, h->subset_variant) > optin) {
     h->subset_variant = 0;  // fewer warps, smaller queues
-    if (class_smem(max_beads, max_cells, 0) > optin) return fail(LHMM_ERR_UNSUPPORTED);
+    if (class_smem(max_beads, max_cells, 0) > optin) h->subset_variant = kFirstGmVariant;
   }
+  if (class_smem(max_beads, max_cells, h->subset_variant) > optin) return fail(LHMM_ERR_UNSUPPORTED);
   // size classes: one per distinct bead count, merged down to at most 12
   std::vector<int> order(nb);
   for (int b = 0; b < nb; ++b) order[b] = b;
@@ -1160,6 +1212,7 @@ extern "C" lhmm_status lhmm_micro_create(const lhmm_dpd_params* params,
       }
       c.variant = default_variant(c.max_beads);
       if (class_smem(c.max_beads, c.max_cells, c.variant) > optin) c.variant = 0;
+      if (class_smem(c.max_beads, c.max_cells, c.variant) > optin) c.variant = kFirstGmVariant;
       h->classes.push_back(std::move(c));
     }
   }
@@ -1177,6 +1230,8 @@ extern "C" lhmm_status lhmm_micro_create(const lhmm_dpd_params* params,
       (e = cudaMalloc(&h->sq_stage, sizeof(double) * 6 * nbx)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaMalloc(&h->work_counter, sizeof(int))) != cudaSuccess)
+    return fail(lhmm_cuda_error(e));
+  if (kVariants[h->subset_variant].gm && (e = ensure_gm(h)) != cudaSuccess)
     return fail(lhmm_cuda_error(e));
   for (auto& c : h->classes) {
     if ((e = cudaMalloc(&c.boxes_d, sizeof(int) * c.boxes.size())) != cudaSuccess ||
@@ -1449,9 +1504,11 @@ extern "C" lhmm_status lhmm_micro_autotune(lhmm_micro_t h, const float* L_dev, i
     a.max_cells = c.max_cells;
     float best = 1e30f;
     int best_v = c.variant;
+    // global-memory variants only for classes no shared-memory variant holds
+    const bool big = !fits_shared(c.max_beads, c.max_cells, optin);
     for (int v = 0; v < kNumVariants; ++v) {
       const size_t sm = class_smem(c.max_beads, c.max_cells, v);
-      if (sm > optin) continue;
+      if (sm > optin || kVariants[v].gm != big) continue;
       const int grid = static_cast<int>(c.boxes.size());
       float ms = 0.f;
       if ((e = launch_variant(v, a, grid, sm, s)) != cudaSuccess ||  // warm-up
@@ -1507,6 +1564,7 @@ extern "C" lhmm_status lhmm_micro_set_variant(lhmm_micro_t h, int cls, int varia
   if (cls < 0 || cls >= static_cast<int>(h->classes.size())) return LHMM_ERR_ARG;
   SizeClass& c = h->classes[cls];
   if (class_smem(c.max_beads, c.max_cells, variant) > max_optin_smem()) return LHMM_ERR_UNSUPPORTED;
+  if (kVariants[variant].gm) LHMM_CK(ensure_gm(h));
   c.variant = variant;
   return LHMM_OK;
 }

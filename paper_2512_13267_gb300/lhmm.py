@@ -337,6 +337,11 @@ class Sph:
         return pos, vel, acc, d
 
 
+# micro kernel variants (include/lhmm.h): threads per block, resident blocks
+# per SM, and whether the box arrays live in device memory instead of shared
+MICRO_VARIANTS = [(256, 4, False), (512, 2, False), (1024, 1, False), (256, 2, False),
+                  (512, 1, False), (512, 1, True), (256, 2, True)]
+
 NOALLOC_MAX_PARTICLES = 65536
 
 

@@ -1,0 +1,157 @@
+"""Boxes held in device memory (kernel variants 5 and 6) instead of one SM's
+shared memory: bit-identical to the shared-memory variant with the same
+threads per block, and parity with the FP64 oracle for boxes too large for
+shared memory (up to the paper's 76 x 76 melt box, Table 2)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2512_13267_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+PAPER_2D = dict(a_ij=25.0, gamma=4.5, sigma=3.0, H_fene=50.0, R0=1.5, dt=0.005)
+FLOW_O = {"periodic": O.FLOW_PERIODIC, "lees_edwards": O.FLOW_LEES_EDWARDS, "afbc": O.FLOW_AFBC}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def _lh():
+    from paper_2512_13267_gb300 import lhmm
+    return lhmm
+
+
+def _batch3d(flow, seed):
+    edges = np.array([3.0, 5.0, 6.0, 7.5, 9.0, 12.0])
+    if flow == "lees_edwards":
+        L = np.zeros((len(edges), 9), np.float32)
+        L[:, 1] = np.linspace(0.05, 0.5, len(edges))
+    else:
+        L = S.random_velocity_gradients(len(edges), seed, rate_range=(0.05, 1.0))
+    return S.make_batch(edges, L, seed, flow=flow)
+
+
+def _run(batch, params, variant, steps):
+    lh = _lh()
+    m = lh.Micro.from_batch(params, batch)
+    for c in range(len(m.plan())):
+        m.set_variant(c, variant)
+    L = torch.from_numpy(batch.L).cuda()
+    st = torch.zeros((batch.n_boxes, 6), dtype=torch.float64, device="cuda")
+    sq = torch.zeros_like(st)
+    m.advance(L, steps, st, sq)
+    status = m.sync(raise_on_error=False)[0]
+    states = [m.get_state(b) for b in range(batch.n_boxes)]
+    m.close()
+    return st.cpu().numpy(), sq.cpu().numpy(), states, status
+
+
+@pytest.mark.parametrize("flow,afbc_mode,dim", [("periodic", 0, 3), ("lees_edwards", 0, 3),
+                                                ("afbc", 0, 3), ("afbc", 1, 3), ("afbc", 0, 2)])
+@pytest.mark.parametrize("smem_v,gm_v", [(4, 5), (3, 6)])
+def test_device_memory_variant_is_bitwise_equal_to_shared(flow, afbc_mode, dim, smem_v, gm_v):
+    lh = _lh()
+    assert lh.MICRO_VARIANTS[smem_v][:2] == lh.MICRO_VARIANTS[gm_v][:2]
+    assert not lh.MICRO_VARIANTS[smem_v][2] and lh.MICRO_VARIANTS[gm_v][2]
+    if dim == 2:
+        edges = np.array([3.0, 8.0, 12.0, 20.0])
+        L = np.zeros((4, 9), np.float32)
+        L[:, 1] = 0.1
+        n = np.rint(4 * edges * edges).astype(int)
+        n -= n % 8
+        batch = S.make_batch(edges, L, 5, flow=flow, chain_len=8, fraction=1.0, n_beads=n, dim=2)
+        params = lh.dpd_params(flow=flow, seed=5, dim=2, afbc_mode=afbc_mode, **PAPER_2D)
+    else:
+        batch = _batch3d(flow, 5)
+        params = lh.dpd_params(flow=flow, seed=5, afbc_mode=afbc_mode)
+    a = _run(batch, params, smem_v, 30)
+    b = _run(batch, params, gm_v, 30)
+    assert a[3] == b[3]
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    for sa, sb in zip(a[2], b[2]):
+        for x, y in zip(sa, sb):
+            assert np.array_equal(np.asarray(x), np.asarray(y))
+
+
+def _oracle_boxes(batch, op):
+    boxes = []
+    for b in range(batch.n_boxes):
+        sl = batch.box_slice(b)
+        ob = O.Box(batch.edges[b], batch.pos[sl], batch.vel[sl], int(batch.n_chains[b]),
+                   batch.chain_len, box_id=b)
+        O.compute_forces(op, ob, batch.L[b])
+        boxes.append(ob)
+    return boxes
+
+
+def _minimage(d, E):
+    return d - E * np.rint(d / E)
+
+
+@pytest.mark.parametrize("flow", ["periodic", "afbc"])
+def test_3d_box_beyond_shared_memory_matches_oracle(flow):
+    # 14^3 box at density 3: 8232 beads, more than one SM's shared memory holds
+    lh = _lh()
+    edges = np.array([14.0, 6.0])
+    L = S.random_velocity_gradients(2, 7, rate_range=(0.1, 0.5))
+    batch = S.make_batch(edges, L, 7, flow=flow)
+    assert batch.n_beads[0] > 5700
+    m = lh.Micro.from_batch(lh.dpd_params(flow=flow, seed=7), batch)
+    op = O.dpd_params(flow_mode=FLOW_O[flow], seed=7)
+    boxes = _oracle_boxes(batch, op)
+    plan = m.plan()
+    assert any(c["max_beads"] == batch.n_beads[0] for c in plan)
+    for b, ob in enumerate(boxes):
+        _, _, f, _, _ = m.get_state(b)
+        assert np.abs(f - ob.force).max() <= 1e-4, (b, np.abs(f - ob.force).max())
+    Lg = torch.from_numpy(batch.L).cuda()
+    st = torch.zeros((2, 6), dtype=torch.float64, device="cuda")
+    m.advance(Lg, 20, st)
+    assert m.sync(raise_on_error=False)[0] == lh.OK
+    got = st.cpu().numpy()
+    for b, ob in enumerate(boxes):
+        ref, _, err = O.advance(op, ob, batch.L[b], 20)
+        assert err == 0
+        pos, _, _, step, _ = m.get_state(b)
+        assert step == 20
+        assert np.abs(_minimage(pos - ob.pos, batch.edges[b][0])).max() <= 1e-3
+        scale = 1.0 + np.abs(ref).max()
+        assert np.abs(got[b] - ref).max() <= 2e-2 * scale, (b, got[b], ref)
+    m.close()
+
+
+def test_paper_76x76_melt_box_matches_oracle():
+    # the paper's micro-domain (Table 2): a 76 x 76 2D melt of N_d = 8 chains
+    # at number density 4 (23 104 beads) under planar shear through the AFBC
+    # shell; it runs in the device-memory variant
+    lh = _lh()
+    edges = np.array([76.0])
+    L = np.zeros((1, 9), np.float32)
+    L[0, 1] = 0.01
+    n = np.array([4 * 76 * 76])
+    batch = S.make_batch(edges, L, 9, flow="afbc", chain_len=8, fraction=1.0, n_beads=n, dim=2)
+    params = lh.dpd_params(flow="afbc", seed=9, dim=2, **PAPER_2D)
+    m = lh.Micro.from_batch(params, batch)
+    assert m.info()[2] == 23104
+    op = O.dpd_params(flow_mode=O.FLOW_AFBC, seed=9, dim=2, **PAPER_2D)
+    (ob,) = _oracle_boxes(batch, op)
+    _, _, f, _, _ = m.get_state(0)
+    assert np.abs(f - ob.force).max() <= 1e-4
+    Lg = torch.from_numpy(batch.L).cuda()
+    st = torch.zeros((1, 6), dtype=torch.float64, device="cuda")
+    m.advance(Lg, 10, st)
+    assert m.sync(raise_on_error=False)[0] == lh.OK
+    ref, _, err = O.advance(op, ob, batch.L[0], 10)
+    assert err == 0
+    pos, vel, _, _, _ = m.get_state(0)
+    assert np.all(vel[:, 2] == 0.0)
+    assert np.abs(_minimage(pos - ob.pos, 76.0)).max() <= 1e-3
+    got = st.cpu().numpy()[0]
+    assert np.abs(got - ref).max() <= 2e-2 * (1.0 + np.abs(ref).max()), (got, ref)
+    m.close()
