@@ -343,6 +343,13 @@ def main():
                 "peak_source": "%d SMs x %d FP32/INT lanes x %.0f MHz (%s sm_max_mhz)"
                                % (N_SM, LANES_PER_SM_CLK, clk_mhz, src),
                 "kernel": "micro_kernel", "algo_ops_per_bead_step": ALGO_OPS_PER_BEAD_STEP}
+    try:  # measured issue rate of the CUDA cores, beside the derived peak
+        f_rate, i_rate = lhmm.issue_rate_probe(iters=200)
+        roofline["peak_probe"] = {"ffma": f_rate / 1e12, "int_xor_add": i_rate / 1e12,
+                                  "unit": "T lane-ops/s",
+                                  "frac_of_ffma_probe": achieved / (f_rate / 1e12)}
+    except Exception as exc:  # pragma: no cover
+        roofline["peak_probe"] = {"error": str(exc)}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,

@@ -1,0 +1,95 @@
+// Issue-rate probe: the achievable lane-operation rate of the CUDA cores,
+// the denominator of the micro kernel's roofline (that kernel is bound by
+// instruction issue, not by memory or tensor cores).  Each thread runs eight
+// independent dependency chains, so every warp scheduler always has an
+// instruction ready; the rate counts only the chain operations.
+#include <cuda_runtime.h>
+
+#include "lhmm_common.cuh"
+
+namespace {
+
+constexpr int kProbeThreads = 512;
+constexpr int kProbeUnroll = 16;
+
+__global__ void __launch_bounds__(kProbeThreads) probe_ffma(int iters, float c, float* sink) {
+  float a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = static_cast<float>(threadIdx.x + k) * 1e-3f;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int r = 0; r < kProbeUnroll; ++r) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) a[k] = fmaf(a[k], c, 1e-7f);
+    }
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  if (s == -1.f) sink[0] = s;  // keeps the chains alive; never true for c in (0, 1)
+}
+
+__global__ void __launch_bounds__(kProbeThreads) probe_int(int iters, unsigned c, unsigned* sink) {
+  unsigned u[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) u[k] = threadIdx.x * 2654435761u + k;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int r = 0; r < kProbeUnroll; ++r) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) u[k] = (u[k] ^ c) + static_cast<unsigned>(2 * k + 1);
+    }
+  }
+  unsigned s = 0u;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s ^= u[k];
+  if (s == 0x12345678u && c == 0u) sink[0] = s;  // c is never 0 here
+}
+
+}  // namespace
+
+extern "C" lhmm_status lhmm_issue_rate_probe(int iters, double* ffma_ops_per_s,
+                                             double* int_ops_per_s, void* stream) {
+  if (iters < 1 || iters > 100000 || !ffma_ops_per_s || !int_ops_per_s) return LHMM_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 0;
+  LHMM_CK(cudaGetDevice(&dev));
+  LHMM_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = sms * 8;
+  void* sink = nullptr;
+  LHMM_CK(cudaMalloc(&sink, 16));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const double threads = static_cast<double>(grid) * kProbeThreads;
+  double best_f = 0.0, best_i = 0.0;
+  cudaError_t e = cudaSuccess;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // first pass warms up
+    float ms = 0.f;
+    probe_ffma<<<grid, kProbeThreads, 0, s>>>(iters, 0.9999f, static_cast<float*>(sink));
+    cudaEventRecord(e0, s);
+    probe_ffma<<<grid, kProbeThreads, 0, s>>>(iters, 0.9999f, static_cast<float*>(sink));
+    cudaEventRecord(e1, s);
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double f = threads * iters * kProbeUnroll * 8 / (ms * 1e-3);  // one FFMA per op
+    cudaEventRecord(e0, s);
+    probe_int<<<grid, kProbeThreads, 0, s>>>(iters, 0x9E3779B9u, static_cast<unsigned*>(sink));
+    cudaEventRecord(e1, s);
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double in = threads * iters * kProbeUnroll * 8 * 2 / (ms * 1e-3);  // xor + add
+    if (rep > 0) {
+      best_f = f > best_f ? f : best_f;
+      best_i = in > best_i ? in : best_i;
+    }
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  if (e != cudaSuccess) return lhmm_cuda_error(e);
+  *ffma_ops_per_s = best_f;
+  *int_ops_per_s = best_i;
+  return LHMM_OK;
+}

@@ -381,3 +381,12 @@ def test_afbc_peculiar_mode_matches_oracle():
         assert np.abs(vel - ob.vel).max() <= 1e-4, (b, np.abs(vel - ob.vel).max())
     assert stepwise_afbc_parity(m, op, batch, 30) <= 10
     m.close()
+
+
+def test_issue_rate_probe_is_near_the_lane_count_times_clock():
+    # the roofline denominator: 152 SMs x 128 lanes x clock (at most ~2.07 GHz)
+    lh = _lh()
+    f, i = lh.issue_rate_probe(iters=50)
+    nominal = 152 * 128 * 2.07e9
+    assert 0.3 * nominal < f < 1.05 * nominal, f
+    assert 0.3 * nominal < i < 1.05 * nominal, i
