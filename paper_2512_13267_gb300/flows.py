@@ -139,3 +139,66 @@ def rpf_paper(F=1e-3, chain_len=8, alpha=1e-4, n_macro=1000, n_avg=300, box_edge
     for o in (cpl, micro, sph):
         o.close()
     return out
+
+
+def rpm_paper_rate(steps=3, warmup=1, chain_len=16, box_edge=76.0, F=1e-3, alpha=1e-4,
+                   eta_s=0.02, c=0.5, distinct_states=64, seed=5):
+    """Macro-steps/s at the scale of the paper's random-porous-medium run
+    (Sec. 6.3): a periodic 12 x 4 box with 17 cylinders at porosity 0.792
+    (synthetic placement: the paper's obstacle table is not available),
+    dh = 1/16, Lucy kernel h = 4 dh, delta_t = 0.125 = 25 DPD steps of 0.005,
+    M = 50 SPH substeps of 2.5e-3, and one 2D melt box of box_edge^2 * 4 beads
+    of N_d = chain_len chains (Table 1 parameters, AFBC) per fluid particle.
+    Boxes start from `distinct_states` different initial states repeated
+    (their random streams differ by box id); this only shortens set-up.
+    Times graph-replayed macro steps after `warmup` untimed ones."""
+    import torch
+    pos, is_wall, Lx, Ly, dh, _, _ = synth.random_porous_medium(dh=1.0 / 16.0, seed=seed)
+    n = pos.shape[0]
+    n_wall = int(is_wall.sum())
+    n_fluid = n - n_wall
+    k_micro = 25
+    M = 50
+    sp = lhmm.sph_params(n, n_wall, Lx=Lx, Ly=Ly, h=4.0 * dh, mass=dh * dh, rho0=1.0, c=c,
+                         theta_pb=0.1, eta_s=eta_s, dt=k_micro * rheometry.PAPER_2D["dt"] / M,
+                         kernel=lhmm.SPH_LUCY, body_force=(F, 0.0),
+                         body_mode=lhmm.SPH_BODY_UNIFORM)
+    sph = lhmm.Sph(sp, pos, np.zeros_like(pos))
+    nb = int(round(4 * box_edge * box_edge))
+    nb -= nb % chain_len
+    batch = synth.make_batch(np.full(n_fluid, box_edge), np.zeros((n_fluid, 9), np.float32),
+                             seed, flow="afbc", chain_len=chain_len, fraction=1.0,
+                             n_beads=np.full(n_fluid, nb), dim=2, with_state=False)
+    reps = -(-n_fluid // distinct_states)
+    ps, vs = [], []
+    for b in range(min(distinct_states, n_fluid)):
+        p, v = synth.initial_box_state(batch.edges[b].astype(np.float64), nb, seed, b,
+                                       L=batch.L[b], flow="afbc", dim=2)
+        ps.append(p)
+        vs.append(v)
+    batch.pos = np.tile(np.concatenate(ps), (reps, 1))[:batch.total_beads]
+    batch.vel = np.tile(np.concatenate(vs), (reps, 1))[:batch.total_beads]
+    t0 = time.perf_counter()
+    micro = lhmm.Micro.from_batch(
+        lhmm.dpd_params(flow="afbc", seed=seed, dim=2, alpha=alpha, **rheometry.PAPER_2D), batch)
+    batch.pos = batch.vel = None
+    L0 = torch.zeros((n_fluid, 9), dtype=torch.float32, device="cuda")
+    micro.autotune(L0, probe_steps=5)
+    cpl = lhmm.Coupled(sph, micro, M, k_micro)
+    t_setup = time.perf_counter() - t0
+    cpl.step(warmup, use_graph=True)
+    rate = _rate(cpl, steps)
+    status = lhmm.status_string(micro.sync(raise_on_error=False)[0])
+    beads = int(batch.total_beads)
+    out = dict(metric="LHMM macro-steps/s (plain DPD closure), paper-scale porous medium",
+               value=rate, unit="macro-steps/s", steps=steps, warmup=warmup,
+               sph_particles=n, fluid_particles=n_fluid, wall_particles=n_wall,
+               sph_substeps=M, micro_steps=k_micro, boxes=n_fluid, beads=beads,
+               bead_steps_per_s=rate * beads * k_micro, s_per_macro_step=1.0 / rate,
+               setup_s=t_setup, plan=micro.plan(), device_status=status,
+               workload="random porous medium 12x4, 17 cylinders, porosity 0.792, dh=1/16 "
+                        "(Lucy h=4dh) x 2D N_d=%d melt boxes of %d beads (AFBC), "
+                        "k'=25, M=50" % (chain_len, nb))
+    for o in (cpl, micro, sph):
+        o.close()
+    return out

@@ -256,6 +256,54 @@ def cylinder_array(n_fluid_target=16384, radius_frac=0.25, wall_layers=None, h_o
     return pos, is_wall, L, dh
 
 
+def random_porous_medium(Ly=4.0, aspect=3.0, dh=1.0 / 16.0, n_obstacles=17, porosity=0.792,
+                         mean_radius=0.425, h_over_dh=4.0, seed=7):
+    """Synthetic stand-in for the paper's random porous medium (Sec. 6.3): a
+    periodic Lx x Ly box (Lx = aspect Ly) with n_obstacles non-overlapping
+    cylinders whose radii scatter by +-25 % around mean_radius, scaled so the
+    solid area gives the stated porosity (the paper's obstacle table is not
+    available).  Lattice particles of spacing dh outside the cylinders are
+    fluid (first); those inside within h = h_over_dh dh of a surface are
+    fixed wall particles (last).  Returns (pos, is_wall, Lx, Ly, dh, centres,
+    radii)."""
+    rng = np.random.default_rng([int(seed), 0x2A9])
+    Lx = aspect * Ly
+    r = mean_radius * (1.0 + 0.25 * rng.uniform(-1.0, 1.0, size=n_obstacles))
+    r *= np.sqrt((1.0 - porosity) * Lx * Ly / (np.pi * np.sum(r ** 2)))
+    centres = np.zeros((n_obstacles, 2))
+    order = np.argsort(-r)  # place the largest first
+    placed = []
+    for k in order:
+        for _ in range(100000):
+            c = rng.uniform([0.0, 0.0], [Lx, Ly])
+            ok = True
+            for j in placed:
+                d = c - centres[j]
+                d -= np.array([Lx, Ly]) * np.rint(d / np.array([Lx, Ly]))
+                if np.hypot(*d) < r[k] + r[j] + 2.0 * dh:
+                    ok = False
+                    break
+            if ok:
+                centres[k] = c
+                placed.append(k)
+                break
+        else:
+            raise RuntimeError("could not place the obstacles")
+    nx, ny = int(round(Lx / dh)), int(round(Ly / dh))
+    pos = sph_lattice(nx, ny, Lx, Ly)
+    depth = np.full(pos.shape[0], -np.inf)  # how far inside the nearest cylinder
+    for c, R in zip(centres, r):
+        d = pos - c
+        d -= np.array([Lx, Ly]) * np.rint(d / np.array([Lx, Ly]))
+        depth = np.maximum(depth, R - np.hypot(d[:, 0], d[:, 1]))
+    fluid = depth <= 0.0
+    wall = (~fluid) & (depth <= h_over_dh * dh)
+    pos = np.concatenate([pos[fluid], pos[wall]], axis=0)
+    is_wall = np.concatenate([np.zeros(int(fluid.sum()), np.int32),
+                              np.ones(int(wall.sum()), np.int32)])
+    return pos, is_wall, Lx, Ly, dh, centres, r
+
+
 def coupled_channel(nx=64, ny=32, Ly=4.0, box_beads=1500, seed=3, c_factor=10.0, U_o=0.25,
                     eta_s=0.1, eta_tot=None, delta_t=0.5):
     """The coupled reverse-Poiseuille workload: an nx x ny SPH channel of height

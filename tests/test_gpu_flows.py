@@ -31,3 +31,14 @@ def test_coupled_rpf_matches_exact_shear_stress():
     pol = np.array(out["sigma_polymer"])
     assert out["polymer_share"] > 0.1
     assert np.all(np.sign(pol[[0, 1, 3, 4]]) == np.sign(ex[[0, 1, 3, 4]]))
+
+
+def test_porous_medium_coupled_step_runs_with_walls():
+    # the paper-scale porous-medium workload at small boxes: 17 obstacles with
+    # wall particles, one 2D melt box per fluid particle, graph-replayed steps
+    from paper_2512_13267_gb300 import flows
+    out = flows.rpm_paper_rate(steps=1, warmup=1, chain_len=8, box_edge=12.0,
+                               distinct_states=8)
+    assert out["device_status"] == "ok"
+    assert out["value"] > 0.0
+    assert out["wall_particles"] > 0 and out["boxes"] == out["fluid_particles"]
