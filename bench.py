@@ -371,6 +371,14 @@ def main():
         line["secondary"] = macro_step_rate()
         from paper_2512_13267_gb300 import flows
         line["rpf_paper"] = flows.rpf_paper_rate()
+        # the paper's largest run (random porous medium, 76 x 76 boxes of
+        # N_d = 16 melt): its 65.7 h for ~1.41e5 SPH steps is 1.68 s per SPH
+        # step, 84 s per macro step of M = 50 substeps, for 12 288 boxes
+        rpm = flows.rpm_paper_rate(steps=3, warmup=1)
+        rpm["paper_s_per_macro_step"] = 1.68 * 50
+        rpm["paper_beads"] = 12288 * 23104
+        rpm["paper_bead_steps_per_s"] = 12288 * 23104 * 25 / (1.68 * 50)
+        line["rpm_paper"] = rpm
     if rank == 0 and not args.no_surrogate and args.uniform_edge <= 0:
         from paper_2512_13267_gb300 import closure
         r = closure.surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, n_eval=60,

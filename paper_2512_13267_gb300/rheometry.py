@@ -27,6 +27,48 @@ def carreau_yasuda(gdot, eta0, eta_inf, lam, a, n):
     return eta_inf + (eta0 - eta_inf) * (1.0 + (lam * g) ** a) ** ((n - 1.0) / a)
 
 
+def fit_carreau_yasuda(gdot, eta, eta_se=None, fix_eta_inf=None):
+    """Least-squares Carreau-Yasuda fit (Sec. 5.1, appendix on the CY model)
+    of eta(gdot), in log eta with weights from the standard errors when given.
+    Returns dict(eta0, eta_inf, lam, a, n, rms_log_residual).  fix_eta_inf
+    pins eta_inf (the plateau at high rates is often outside the data)."""
+    from scipy.optimize import least_squares
+    g = np.asarray(gdot, dtype=np.float64)
+    y = np.asarray(eta, dtype=np.float64)
+    w = np.ones_like(y) if eta_se is None else y / np.maximum(np.asarray(eta_se, np.float64),
+                                                              1e-3 * y)
+    w = w / w.mean()
+
+    def unpack(q):
+        eta0, lam, a, n = np.exp(q[0]), np.exp(q[1]), q[2], q[3]
+        eta_inf = fix_eta_inf if fix_eta_inf is not None else np.exp(q[4]) * eta0
+        return eta0, eta_inf, lam, a, n
+
+    def resid(q):
+        eta0, eta_inf, lam, a, n = unpack(q)
+        return w * (np.log(carreau_yasuda(g, eta0, eta_inf, lam, a, n)) - np.log(y))
+
+    q0 = [np.log(y.max() * 1.2), np.log(1.0 / np.median(g)), 1.0, 0.4]
+    lo = [np.log(y.max() * 0.5), np.log(1e-2 / g.max()), 0.2, 0.0]
+    hi = [np.log(y.max() * 20.0), np.log(1e3 / g.min()), 3.0, 0.99]
+    if fix_eta_inf is None:
+        q0.append(np.log(0.05))
+        lo.append(np.log(1e-4))
+        hi.append(np.log(0.5))
+    best = None
+    for lam0 in (0.3, 1.0, 3.0):  # a few starts in lambda
+        q = list(q0)
+        q[1] = np.log(lam0 / np.median(g))
+        q = np.clip(q, np.array(lo) + 1e-9, np.array(hi) - 1e-9)
+        r = least_squares(resid, q, bounds=(lo, hi))
+        if best is None or r.cost < best.cost:
+            best = r
+    eta0, eta_inf, lam, a, n = unpack(best.x)
+    rms = float(np.sqrt(np.mean((best.fun / w) ** 2)))
+    return dict(eta0=float(eta0), eta_inf=float(eta_inf), lam=float(lam), a=float(a), n=float(n),
+                rms_log_residual=rms)
+
+
 def melt_viscosity(chain_len, shear_rates, replicas=32, edge=20.0, equil_time=None,
                    sample_time=None, call_steps=1000, seed=11, dpd_on_bonded=1,
                    exclude_bonds=0):
@@ -168,8 +210,12 @@ def planar_extension(chain_len, rates, replicas=32, edge=36.0, equil_time=None,
     else:
         etaP = (mean[:, :, 0] - mean[:, :, 1]) / rates[:, None]
     m.close()
-    return dict(chain_len=chain_len, rates=rates.tolist(), replicas=replicas, edge=edge,
-                mode=mode, afbc_mode=afbc_mode, beads_per_box=n,
-                eta_P=etaP.mean(axis=1).tolist(),
-                eta_P_se=(etaP.std(axis=1, ddof=1) / np.sqrt(replicas)).tolist(),
-                wall_s=time.perf_counter() - t0, device_status=status)
+    se = lambda x: (x.std(axis=1, ddof=1) / np.sqrt(replicas)).tolist()
+    out = dict(chain_len=chain_len, rates=rates.tolist(), replicas=replicas, edge=edge,
+               mode=mode, afbc_mode=afbc_mode, beads_per_box=n,
+               eta_P=etaP.mean(axis=1).tolist(), eta_P_se=se(etaP),
+               wall_s=time.perf_counter() - t0, device_status=status)
+    if mode == "shear":  # first normal stress coefficient psi_1 = N_1 / gdot^2
+        psi1 = (mean[:, :, 0] - mean[:, :, 1]) / rates[:, None] ** 2
+        out.update(psi1=psi1.mean(axis=1).tolist(), psi1_se=se(psi1))
+    return out

@@ -28,3 +28,24 @@ def test_random_porous_medium_geometry():
     # walls come last; the lattice fluid fraction is close to the porosity
     assert np.all(np.diff(is_wall) >= 0)
     assert abs(fluid.sum() / ((Lx / dh) * (Ly / dh)) - 0.792) < 0.01
+
+
+def test_carreau_yasuda_fit_recovers_known_parameters():
+    # data drawn from the paper's N_d = 8 curve (its CY table) at 8 rates,
+    # 1 % noise: the fit recovers eta0 and the curve; lambda trades off
+    # against n and eta_inf over two decades of rate, so only its scale is
+    # fixed by such data
+    from paper_2512_13267_gb300 import rheometry as R
+    rng = np.random.default_rng(0)
+    g = np.array([0.0005, 0.001, 0.002, 0.005, 0.01, 0.02, 0.05, 0.1])
+    true = R.carreau_yasuda(g, 34.29, 3.15, 89.75, 0.95, 0.37)
+    eta = true * (1 + 0.01 * rng.standard_normal(8))
+    fit = R.fit_carreau_yasuda(g, eta, 0.01 * eta)
+    assert abs(fit["eta0"] / 34.29 - 1) < 0.1, fit
+    assert 0.5 < fit["lam"] / 89.75 < 2.0, fit
+    assert fit["rms_log_residual"] < 0.03
+    curve = R.carreau_yasuda(g, fit["eta0"], fit["eta_inf"], fit["lam"], fit["a"], fit["n"])
+    assert np.all(np.abs(curve / true - 1) < 0.03)
+    # a Newtonian plateau is a flat fit
+    flat = R.fit_carreau_yasuda(g, np.full(8, 5.0))
+    assert abs(flat["eta0"] - 5.0) < 0.05 and abs(R.carreau_yasuda(0.1, flat["eta0"], flat["eta_inf"], flat["lam"], flat["a"], flat["n"]) - 5.0) < 0.05
