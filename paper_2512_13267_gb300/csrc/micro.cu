@@ -13,13 +13,15 @@
 //   C  sums DPD conservative, dissipative and random pair forces (Eqs.
 //      conservative, dissipative, random) over the upper half of the 27
 //      neighbour cells, each neighbour row cut to the x window that the
-//      bead's y, z distance to the row leaves inside rc, plus the FENE bonds
-//      (Eq. fene_force), accumulating the pair virial of the IK potential
-//      stress (Eq. potential_stress) with the core bond fraction;
-//   D  half-kicks, imposes v = lambda* L r' on the AFBC BC shell (Eq.
-//      micro_bc), accumulates the IK kinetic stress (Eq. kinetic_stress) and
-//      block-reduces the step's stress; the time average (N'_t = k') is kept
-//      in FP64.
+//      bead's y, z distance to the row leaves inside rc, accumulating the
+//      pair virial of the IK potential stress (Eq. potential_stress) with
+//      the core bond fraction;
+//   D  per bead: adds its FENE bonds (Eq. fene_force; each bond is computed
+//      by both of its beads, its virial by the lower one), half-kicks,
+//      imposes v = lambda* L r' on the AFBC BC shell (Eq. micro_bc) and
+//      accumulates the IK kinetic stress (Eq. kinetic_stress); then the
+//      block reduces the step's stress; the time average (N'_t = k') is
+//      kept in FP64.
 // Each pair is evaluated once (Newton's third law); pair forces accumulate in
 // 2^-18 fixed point with integer shared-memory atomics, which is exact and
 // order-independent, so a step is bit-reproducible.  The random term
@@ -675,75 +677,90 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
     __syncwarp();
     if (lane < count) eval_pair(queue[lane]);
     __syncthreads();
-    for (int i = tid; i < N; i += T) {  // fixed point -> FP32
-      fx[i] = static_cast<float>(qfx[i]) * kFixInv;
-      fy[i] = static_cast<float>(qfy[i]) * kFixInv;
-      fz[i] = static_cast<float>(qfz[i]) * kFixInv;
-    }
-    __syncthreads();
-    // FENE bonds (k, k+1) inside a chain, attractive (Eq. fene_force); even
-    // then odd k so that no bead takes two bonds in one pass (plain adds,
-    // fixed order)
-    for (int par = 0; par < 2; ++par) {
-      for (int i = 2 * tid + par; i + 1 < sB.n_poly; i += 2 * T) {
-        if (((i + 1) % A.chain_len) == 0) continue;
-        const int j = i + 1;
-        int cx, cy, cz, cxj, cyj, czj;
-        cell_coords(cellid[i], nx, nxy, inx, inxy, cx, cy, cz);
-        cell_coords(cellid[j], nx, nxy, inx, inxy, cxj, cyj, czj);
-        float rx = static_cast<float>(cx - cxj) * wx + (ox[i] - ox[j]);
-        float ry = static_cast<float>(cy - cyj) * wy + (oy[i] - oy[j]);
-        float rz = static_cast<float>(cz - czj) * wz + (oz[i] - oz[j]);
-        if (ry > hy) {
-          ry -= sB.len[1];
-          if (le) rx -= le_off;
-        } else if (ry < -hy) {
-          ry += sB.len[1];
-          if (le) rx += le_off;
-        }
-        rx -= sB.len[0] * rintf(rx / sB.len[0]);
-        if (rz > hz) rz -= sB.len[2];
-        else if (rz < -hz) rz += sB.len[2];
-        float x = (rx * rx + ry * ry + rz * rz) * A.inv_R0sq;
-        if (!(x < 1.f)) {
-          status |= LHMM_BOX_BOND_OVERSTRETCH;
-          x = 0.99f;
-        }
-        const float cf = -A.H / (1.f - x);
-        const float Fx = cf * rx, Fy = cf * ry, Fz = cf * rz;
-        fx[i] += Fx;
-        fy[i] += Fy;
-        fz[i] += Fz;
-        fx[j] -= Fx;
-        fy[j] -= Fy;
-        fz[j] -= Fz;
-        float wgt = 1.f;
-        if (afbc) {  // a bond is shorter than R0
-          const float rpx = static_cast<float>(cx) * wx + ox[i] - hx;
-          const float rpy = static_cast<float>(cy) * wy + oy[i] - hy;
-          const float rpz = static_cast<float>(cz) * wz + oz[i] - hz;
-          const float m = fmaxf(fabsf(rpx) - sB.half_core[0],
-                                fmaxf(fabsf(rpy) - sB.half_core[1], fabsf(rpz) - sB.half_core[2]));
-          if (m >= A.R0) wgt = 0.f;
-          else if (m >= -A.R0)
-            wgt = seg_fraction(rpx, rpy, rpz, rpx - rx, rpy - ry, rpz - rz, sB.half_core);
-        }
-        W[0] += wgt * Fx * rx;
-        W[1] += wgt * Fy * ry;
-        W[2] += wgt * Fz * rz;
-        W[3] += wgt * Fx * ry;
-        W[4] += wgt * Fx * rz;
-        W[5] += wgt * Fy * rz;
+    // FENE bonds (k, k+1) inside a chain, attractive (Eq. fene_force): the
+    // bond vector and force of bond k, computed the same way by both of its
+    // beads, so each bead sums its own forces without atomics or a barrier
+    auto fene = [&](int k, float& Fx, float& Fy, float& Fz, float& rx, float& ry, float& rz,
+                    int& cxk, int& cyk, int& czk) {
+      const int j = k + 1;
+      int cxj, cyj, czj;
+      cell_coords(cellid[k], nx, nxy, inx, inxy, cxk, cyk, czk);
+      cell_coords(cellid[j], nx, nxy, inx, inxy, cxj, cyj, czj);
+      rx = static_cast<float>(cxk - cxj) * wx + (ox[k] - ox[j]);
+      ry = static_cast<float>(cyk - cyj) * wy + (oy[k] - oy[j]);
+      rz = static_cast<float>(czk - czj) * wz + (oz[k] - oz[j]);
+      if (ry > hy) {
+        ry -= sB.len[1];
+        if (le) rx -= le_off;
+      } else if (ry < -hy) {
+        ry += sB.len[1];
+        if (le) rx += le_off;
       }
-      __syncthreads();
-    }
-    if (A.init_forces) break;
-
-    // ---- D: second half kick, AFBC imposition, IK kinetic part, reduction
+      rx -= sB.len[0] * rintf(rx / sB.len[0]);
+      if (rz > hz) rz -= sB.len[2];
+      else if (rz < -hz) rz += sB.len[2];
+      float x = (rx * rx + ry * ry + rz * rz) * A.inv_R0sq;
+      if (!(x < 1.f)) {
+        status |= LHMM_BOX_BOND_OVERSTRETCH;
+        x = 0.99f;
+      }
+      const float cf = -A.H / (1.f - x);
+      Fx = cf * rx;
+      Fy = cf * ry;
+      Fz = cf * rz;
+    };
+    // ---- D: per bead: pair forces (fixed point -> FP32) plus its bonds,
+    // second half kick, AFBC imposition, IK kinetic part
     for (int i = tid; i < N; i += T) {
-      float v0 = vx[i] + A.hdt_m * fx[i];
-      float v1 = vy[i] + A.hdt_m * fy[i];
-      float v2 = vz[i] + A.hdt_m * fz[i];
+      float f0 = static_cast<float>(qfx[i]) * kFixInv;
+      float f1 = static_cast<float>(qfy[i]) * kFixInv;
+      float f2 = static_cast<float>(qfz[i]) * kFixInv;
+      if (i < sB.n_poly) {
+        const int c = i % A.chain_len;
+        float up0 = 0.f, up1 = 0.f, up2 = 0.f, dn0 = 0.f, dn1 = 0.f, dn2 = 0.f;
+        if (c + 1 < A.chain_len) {  // bond (i, i+1): +F on i, and its virial
+          float Fx, Fy, Fz, rx, ry, rz;
+          int cxk, cyk, czk;
+          fene(i, Fx, Fy, Fz, rx, ry, rz, cxk, cyk, czk);
+          up0 = Fx; up1 = Fy; up2 = Fz;
+          float wgt = 1.f;
+          if (afbc) {  // a bond is shorter than R0
+            const float rpx = static_cast<float>(cxk) * wx + ox[i] - hx;
+            const float rpy = static_cast<float>(cyk) * wy + oy[i] - hy;
+            const float rpz = static_cast<float>(czk) * wz + oz[i] - hz;
+            const float m = fmaxf(fabsf(rpx) - sB.half_core[0],
+                                  fmaxf(fabsf(rpy) - sB.half_core[1], fabsf(rpz) - sB.half_core[2]));
+            if (m >= A.R0) wgt = 0.f;
+            else if (m >= -A.R0)
+              wgt = seg_fraction(rpx, rpy, rpz, rpx - rx, rpy - ry, rpz - rz, sB.half_core);
+          }
+          W[0] += wgt * Fx * rx;
+          W[1] += wgt * Fy * ry;
+          W[2] += wgt * Fz * rz;
+          W[3] += wgt * Fx * ry;
+          W[4] += wgt * Fx * rz;
+          W[5] += wgt * Fy * rz;
+        }
+        if (c > 0) {  // bond (i-1, i): -F on i
+          float Fx, Fy, Fz, rx, ry, rz;
+          int cxk, cyk, czk;
+          fene(i - 1, Fx, Fy, Fz, rx, ry, rz, cxk, cyk, czk);
+          dn0 = Fx; dn1 = Fy; dn2 = Fz;
+        }
+        // bonds starting at an even bead first, then those at an odd bead
+        if ((i & 1) == 0) {
+          if (c + 1 < A.chain_len) { f0 += up0; f1 += up1; f2 += up2; }
+          if (c > 0) { f0 -= dn0; f1 -= dn1; f2 -= dn2; }
+        } else {
+          if (c > 0) { f0 -= dn0; f1 -= dn1; f2 -= dn2; }
+          if (c + 1 < A.chain_len) { f0 += up0; f1 += up1; f2 += up2; }
+        }
+      }
+      fx[i] = f0; fy[i] = f1; fz[i] = f2;
+      if (A.init_forces) continue;
+      float v0 = vx[i] + A.hdt_m * f0;
+      float v1 = vy[i] + A.hdt_m * f1;
+      float v2 = vz[i] + A.hdt_m * f2;
       int cx, cy, cz;
       cell_coords(cellid[i], nx, nxy, inx, inxy, cx, cy, cz);
       const float rpx = static_cast<float>(cx) * wx + ox[i] - hx;
@@ -776,6 +793,10 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
         W[4] += A.mass * d0 * d2;
         W[5] += A.mass * d1 * d2;
       }
+    }
+    if (A.init_forces) {
+      __syncthreads();
+      break;
     }
     if (PEC && afbc) {
       __syncthreads();
