@@ -7,9 +7,11 @@
 // and is written back once, so HBM traffic is amortised over k' and the
 // kernel is bound by on-chip arithmetic.  Every step the block
 //   A  half-kicks and drifts its beads, re-normalising cell-relative offsets
-//      and applying Lees-Edwards re-entry (Sec. 2.3 VV; coupling Step 3);
-//   B  rebuilds a counting-sort cell list (cells >= rc wide) ordered by
-//      (x, id) inside each cell, so every row of cells is sorted by x;
+//      and applying Lees-Edwards re-entry (Sec. 2.3 VV; coupling Step 3),
+//      and counts each bead into its cell;
+//   B  turns the counts into a counting-sort cell list (cells >= rc wide)
+//      ordered by (x, id) inside each cell, so every row of cells is sorted
+//      by x;
 //   C  sums DPD conservative, dissipative and random pair forces (Eqs.
 //      conservative, dissipative, random) over the upper half of the 27
 //      neighbour cells, each neighbour row cut to the x window that the
@@ -292,6 +294,15 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
   // would otherwise hold four registers of every thread across the step loop
   double* acc = reinterpret_cast<double*>(red + kRedFloats);
   if (tid < 12) acc[tid] = 0.0;
+  // cell counters start at zero; each step's cell pass resets them after use
+  for (int c = tid; c < (C + 1) / 2; c += T) cnt32[c] = 0u;
+  __syncthreads();
+  // a bead's rank in its cell (counting sort) goes to its force word, which
+  // is free until the pair pass and reset to zero when the bead is placed
+  auto count_in_cell = [&](int i, int c) {
+    const unsigned old = atomicAdd(&cnt32[c >> 1], (c & 1) ? 65536u : 1u);
+    qfx[i] = (c & 1) ? static_cast<int>(old >> 16) : static_cast<int>(old & 0xffffu);
+  };
 
   const int total_steps = A.init_forces ? 1 : A.n_steps;
   for (int s = 0; s < total_steps; ++s) {
@@ -353,24 +364,19 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
         }
         ox[i] = o0; oy[i] = o1; oz[i] = o2;
         vx[i] = v0; vy[i] = v1; vz[i] = v2;
-        fx[i] = 0.f; fy[i] = 0.f; fz[i] = 0.f;  // zero bits: fixed-point zero for C
-        cellid[i] = static_cast<unsigned short>(cx + nx * (cy + ny * cz));
+        fy[i] = 0.f; fz[i] = 0.f;  // zero bits: fixed-point zero for C
+        const int cell = cx + nx * (cy + ny * cz);
+        cellid[i] = static_cast<unsigned short>(cell);
+        count_in_cell(i, cell);
       }
     } else {
       for (int i = tid; i < N; i += T) {
-        fx[i] = 0.f; fy[i] = 0.f; fz[i] = 0.f;
+        fy[i] = 0.f; fz[i] = 0.f;
+        count_in_cell(i, cellid[i]);
       }
     }
-    for (int c = tid; c < (C + 1) / 2; c += T) cnt32[c] = 0u;  // counters 0..C-1
     __syncthreads();
-    // ---- B: counting sort by cell (a bead's rank in its cell is kept in its
-    // force word, which is free until phase C and reset to zero here)
-    for (int i = tid; i < N; i += T) {
-      const int c = cellid[i];
-      const unsigned old = atomicAdd(&cnt32[c >> 1], (c & 1) ? 65536u : 1u);
-      qfx[i] = (c & 1) ? static_cast<int>(old >> 16) : static_cast<int>(old & 0xffffu);
-    }
-    __syncthreads();
+    // ---- B: counting sort by cell (ranks counted in A)
     {
       const int per = (C + T - 1) / T;
       const int c0 = min(tid * per, C), c1 = min(c0 + per, C);
@@ -408,6 +414,7 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
       qfx[i] = 0;  // fixed-point zero for C
     }
     __syncthreads();
+    for (int c = tid; c < (C + 1) / 2; c += T) cnt32[c] = 0u;  // for the next step
     for (int c = tid; c < C; c += T) {  // ascending (x, id) inside each cell
       const int s0 = cstart[c], s1 = cstart[c + 1];
       for (int p = s0 + 1; p < s1; ++p) {
@@ -815,7 +822,9 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
       acc[tid] += pi;
       acc[6 + tid] += pi * pi;
     }
-    __syncthreads();
+    // no barrier here: `red` is next written by the cell scan, after the
+    // barrier that ends the next step's drift, which threads 0..5 reach only
+    // after this sum
   }
 
   // write back

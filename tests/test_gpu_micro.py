@@ -390,3 +390,28 @@ def test_issue_rate_probe_is_near_the_lane_count_times_clock():
     nominal = 152 * 128 * 2.07e9
     assert 0.3 * nominal < f < 1.05 * nominal, f
     assert 0.3 * nominal < i < 1.05 * nominal, i
+
+
+@pytest.mark.parametrize("afbc_mode", [0, 1])
+@pytest.mark.parametrize("flow", ["periodic", "afbc"])
+def test_one_call_of_k_steps_equals_k_calls_of_one_step(flow, afbc_mode):
+    # state carried across steps inside one launch must equal the state
+    # carried through device memory between launches, bit for bit (a missing
+    # barrier between the steps of one call would show here)
+    if flow == "periodic" and afbc_mode == 1:
+        pytest.skip("afbc_mode applies to AFBC boxes")
+    lh = _lh()
+    batch = _ragged_afbc_batch(seed=17)
+    L = torch.from_numpy(batch.L).cuda()
+    st = torch.zeros((batch.n_boxes, 6), dtype=torch.float64, device="cuda")
+    a = lh.Micro.from_batch(lh.dpd_params(flow=flow, seed=17, afbc_mode=afbc_mode), batch)
+    b = lh.Micro.from_batch(lh.dpd_params(flow=flow, seed=17, afbc_mode=afbc_mode), batch)
+    a.advance(L, 12, st)
+    for _ in range(12):
+        b.advance(L, 1, st)
+    assert a.sync(raise_on_error=False)[0] == b.sync(raise_on_error=False)[0]
+    for box in range(batch.n_boxes):
+        for x, y in zip(a.get_state(box)[:4], b.get_state(box)[:4]):
+            assert np.array_equal(np.asarray(x), np.asarray(y)), box
+    a.close()
+    b.close()
