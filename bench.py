@@ -40,10 +40,10 @@ ALGO_OPS_PER_BEAD_STEP = PAIRS_PER_BEAD * OPS_PER_PAIR + OPS_PER_BEAD
 N_SM = 152
 LANES_PER_SM_CLK = 128
 # DRAM bytes (read + write) per bead and call of micro_kernel, from the ncu
-# capture in profiles/micro_kernel_e12_304box_full.md (75.78 + 14.79 MB for
+# capture in profiles/micro_kernel_e12_304box_full.md (76.02 + 16.07 MB for
 # 1,575,936 beads); the kernel reads and writes box state once per call, so
 # traffic scales with beads, not with DPD steps.
-DRAM_BYTES_PER_BEAD_CALL = 90.569e6 / 1575936
+DRAM_BYTES_PER_BEAD_CALL = 92.087e6 / 1575936
 
 
 def _peaks():

@@ -116,7 +116,12 @@ const char* lhmm_status_string(lhmm_status s);
  * as float), and
  * compute the initial forces F(0) under the velocity gradients L0_host (host,
  * n_boxes x 9, or NULL for zero; Lees-Edwards boxes need it for the velocity
- * jump of their sliding images).  Synchronous.  Allocates all device state. */
+ * jump of their sliding images).  Synchronous.  Allocates all device state,
+ * including the per-box scratch of the device-memory kernel variants when
+ * the largest box does not fit one SM's shared memory.  Returns
+ * LHMM_ERR_ARG for bad sizes or parameters, LHMM_ERR_UNSUPPORTED for a box
+ * of more than 65 535 cells or a Lees-Edwards box of more than 60 cells in
+ * x (16-bit cell ids and the 8-bit image offset of a queued pair). */
 lhmm_status lhmm_micro_create(const lhmm_dpd_params* params, const lhmm_batch_desc* batch,
                               const double* pos0_host, const float* vel0_host,
                               const float* L0_host, void* stream, lhmm_micro_t* out);
