@@ -315,7 +315,7 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
       le_off -= floorf(le_off / sB.len[0]) * sB.len[0];
       if (le_off >= sB.len[0]) le_off -= sB.len[0];
     }
-    // ---- A: half kick + drift + cell re-normalisation
+    // ---- A: half kick + drift + cell re-normalisation + count into cells
     if (kick) {
       for (int i = tid; i < N; i += T) {
         float v0 = vx[i] + A.hdt_m * fx[i];
@@ -439,7 +439,8 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
     // (dz, dy) = (0,+1), (+1,-1), (+1,0), (+1,+1)), cut to the x window that
     // can hold partners within r_c.  Pairs inside r_c go to the warp's queue
     // and are evaluated 32 at a time with every lane busy; f_i += F_ij and
-    // f_j -= F_ij with shared-memory atomics.
+    // f_j -= F_ij with integer atomics on the box's force words (shared
+    // memory, or the box's device scratch in the GM variants).
     float W[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     auto eval_pair = [&](unsigned long long e) {
       const int i = static_cast<int>(e & 0xffffu), j = static_cast<int>((e >> 16) & 0xffffu);
