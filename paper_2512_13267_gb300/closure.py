@@ -131,11 +131,45 @@ def _channel(seed, alpha, U_o, c_factor, eta_s, k_micro, dt_dpd, members, closur
                          body_force=(sph_cfg["body_force"], 0.0),
                          body_mode=lhmm.SPH_BODY_REVERSE_POISEUILLE)
     sph = lhmm.Sph(sp, sph_cfg["pos"], sph_cfg["vel"])
-    micro = lhmm.Micro.from_batch(lhmm.dpd_params(flow="afbc", seed=seed, alpha=alpha), batch)
+    params = lhmm.dpd_params(flow="afbc", seed=seed, alpha=alpha)
+    micro = lhmm.Micro.from_batch(params, batch)
     cpl = lhmm.Coupled(sph, micro, M, k_micro)
+    cpl.micro_batch, cpl.micro_params, cpl.k_micro = batch, params, k_micro
     clo = lhmm.Closure(members=members, in_dim=N_IN, hidden=256, n_hidden=4, out_dim=N_OUT,
                        seed=closure_seed)
     return cpl, clo, sph_cfg, M
+
+
+def onpolicy_pairs(gated, shadow, n_steps, absolute=False, lockstep=()):
+    """Training pairs from the flow the gated system actually produces
+    (dataset aggregation): `shadow` is a micro batch holding the same boxes,
+    started from the gated system's micro state, that runs DPD for every
+    particle under the gradients the gated macro step exports.  Its stress is
+    the label the closure should have given each particle in that flow,
+    including the trusted ones.  Systems in `lockstep` take one plain step per
+    gated step."""
+    import torch
+    nb = gated.n_boxes
+    for b in range(nb):
+        pos, vel, frc, step, le = gated.micro.get_state(b)
+        shadow.set_state(b, pos, vel, frc, step, le)
+    Ld = torch.zeros((nb, 9), dtype=torch.float32, device="cuda")
+    st = torch.zeros((nb, 6), dtype=torch.float64, device="cuda")
+    Xs, Ts = [], []
+    for _ in range(n_steps):
+        for sysm in lockstep:
+            sysm.step(1, use_graph=True)
+        gated.step(1, use_graph=True)
+        X = gated.closure_inputs()
+        L, _ = gated.exchange()
+        Ld.copy_(torch.from_numpy(L))
+        shadow.advance(Ld, gated.k_micro, st)
+        T = st.cpu().numpy()[:, STRESS_COLS].astype(np.float32)
+        if not absolute:
+            T = T - X[:, 64:67]
+        Xs.append(X)
+        Ts.append(T)
+    return np.concatenate(Xs), np.concatenate(Ts)
 
 
 def _rate(cpl, steps):
@@ -156,7 +190,8 @@ def surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, batch=4096, n_eval
                        threshold=0.02, audit_every=50, timing_steps=10, seed=3, alpha=0.01,
                        U_o=0.25, c_factor=10.0, eta_s=0.1, k_micro=50, dt_dpd=0.01, members=5,
                        lr=1e-3, weight_decay=1e-4, cosine=False, nbins=16, thresholds=None,
-                       noise_floor=False, absolute=False, warmup_steps=-1, calibrated=False):
+                       noise_floor=False, absolute=False, warmup_steps=-1, calibrated=False,
+                       onpolicy_rounds=0, onpolicy_steps=50, onpolicy_train_steps=None):
     """Plain LHMM vs surrogate-gated LHMM on the coupled reverse-Poiseuille
     channel.  Two identical systems run the same `warm + n_data` plain steps
     (one collects training pairs); the ensemble trains on the GPU; then both run
@@ -168,7 +203,11 @@ def surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, batch=4096, n_eval
     the same windows: the error two plain runs already differ by.  Returns a
     dict of rates, errors and counts.  `absolute` trains and gates the
     closure on the stress itself from the gradient history (no stress input)
-    instead of the increment."""
+    instead of the increment.  `onpolicy_rounds` > 0 then runs that many
+    rounds of `onpolicy_steps` gated steps whose shadow-DPD labels
+    (`onpolicy_pairs`) join the training set before the closure trains
+    again (onpolicy_train_steps, default train_steps) and, if `calibrated`,
+    is recalibrated on the newest on-policy pairs."""
     kw = dict(alpha=alpha, U_o=U_o, c_factor=c_factor, eta_s=eta_s, k_micro=k_micro,
               dt_dpd=dt_dpd, members=members)
     A, clo_a, cfg, M = _channel(seed=seed, closure_seed=1, **kw)
@@ -199,6 +238,25 @@ def surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, batch=4096, n_eval
         a_c, c_c = calibrate(clo_b, X[n_fit:], T[n_fit:], scale)
         calib = dict(a=a_c.tolist(), c=c_c.tolist())
     B.enable_gate(True)
+    n_onpolicy = 0
+    if onpolicy_rounds > 0:
+        shadow = lhmm.Micro.from_batch(B.micro_params, B.micro_batch)
+        lock = [A] + ([C] if C is not None else [])
+        for _ in range(onpolicy_rounds):
+            B.set_gate(threshold, audit_every, absolute, warmup_steps)
+            Xo, To = onpolicy_pairs(B, shadow, onpolicy_steps, absolute, lockstep=lock)
+            n_onpolicy += Xo.shape[0]
+            n_new = Xo.shape[0] if not calibrated else (Xo.shape[0] * 9 // 10)
+            X = np.concatenate([X[:n_fit], Xo[:n_new]])
+            T = np.concatenate([T[:n_fit], To[:n_new]])
+            n_fit = X.shape[0]
+            h2, t2 = train(clo_b, X, T, onpolicy_train_steps or train_steps, batch=batch, lr=lr,
+                           weight_decay=weight_decay, seed=1 + n_onpolicy, cosine=cosine)
+            t_train += t2
+            if calibrated:
+                a_c, c_c = calibrate(clo_b, Xo[n_new:], To[n_new:], scale)
+                calib = dict(a=a_c.tolist(), c=c_c.tolist())
+        shadow.close()
     Ly = cfg["Ly"]
     windows = []
     for thr in (thresholds if thresholds else [threshold]):
@@ -241,6 +299,7 @@ def surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, batch=4096, n_eval
         / max(1, (gs["gated_steps"] - gs0["gated_steps"]) * B.n_boxes),
         audit_rel_err=float(np.sqrt(gs["audit_err2"] / max(gs["audit_ref2"], 1e-300))),
         train_pairs=int(X.shape[0]), train_steps=train_steps, batch=batch,
+        onpolicy_rounds=onpolicy_rounds, onpolicy_pairs=n_onpolicy,
         train_loss_first=[float(x) for x in hist[0]] if hist else None,
         train_loss_last=[float(x) for x in hist[-1]] if hist else None,
         t_data_s=t_data, t_train_s=t_train, sph_substeps=M, micro_steps=k_micro,

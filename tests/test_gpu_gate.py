@@ -30,6 +30,8 @@ def _system(seed=7, nx=8, ny=8, Ly=1.0):
     sph = lh.Sph(sp, pos, vel)
     micro = lh.Micro.from_batch(lh.dpd_params(flow="afbc", seed=5, alpha=0.05), batch)
     cpl = lh.Coupled(sph, micro, 4, 6)
+    cpl.micro_batch, cpl.micro_params, cpl.k_micro = batch, lh.dpd_params(
+        flow="afbc", seed=5, alpha=0.05), 6
     clo = lh.Closure(members=5, in_dim=67, hidden=256, n_hidden=4, out_dim=3, seed=2)
     clo.set_normalization(np.zeros(67), np.ones(67), np.full(3, 1e-3))
     return cpl, clo
@@ -154,3 +156,23 @@ def test_frozen_boxes_warm_up_when_they_return(warm, expect_extra):
     cpl.step(1, use_graph=False)          # no box was frozen in between: no warm-up
     again = [cpl.micro.get_state(b)[3] for b in range(cpl.n_boxes)]
     assert all(a - b == 6 for a, b in zip(again, after))
+
+
+def test_onpolicy_labels_are_the_dpd_stress_when_every_box_runs_dpd():
+    # with a zero threshold every box runs DPD in the gated step, so the
+    # shadow batch (cloned state, same gradients) must give the same stress
+    from paper_2512_13267_gb300 import closure
+    from paper_2512_13267_gb300 import lhmm as lh
+    cpl, clo = _system(seed=11)
+    cpl.set_closure(clo, threshold=0.0)
+    cpl.step(2, use_graph=True)
+    cpl.enable_gate(True)
+    shadow = lh.Micro.from_batch(cpl.micro_params, cpl.micro_batch)
+    X, T = closure.onpolicy_pairs(cpl, shadow, 3, absolute=True)
+    n = cpl.n_boxes
+    assert X.shape == (3 * n, 67) and T.shape == (3 * n, 3)
+    _, st = cpl.exchange()
+    ref = st[:, [0, 3, 1]]
+    assert np.abs(T[-n:] - ref).max() <= 1e-5 * (1.0 + np.abs(ref).max())
+    for o in (shadow, cpl, clo):
+        o.close()
