@@ -155,3 +155,37 @@ def test_paper_76x76_melt_box_matches_oracle():
     got = st.cpu().numpy()[0]
     assert np.abs(got - ref).max() <= 2e-2 * (1.0 + np.abs(ref).max()), (got, ref)
     m.close()
+
+
+@pytest.mark.parametrize("afbc_mode", [0, 1])
+def test_device_list_advance_of_large_boxes_equals_plain_advance(afbc_mode):
+    # the persistent launch over a device-side box list (what a gated
+    # coupled step uses) in the device-memory variant: same states and
+    # stresses as the per-class launch, bit for bit
+    lh = _lh()
+    edges = np.array([40.0, 44.0, 42.0])
+    L = np.zeros((3, 9), np.float32)
+    L[:, 1] = [0.02, 0.05, 0.1]
+    n = np.rint(4 * edges * edges).astype(int)
+    n -= n % 8
+    batch = S.make_batch(edges, L, 13, flow="afbc", chain_len=8, fraction=1.0, n_beads=n, dim=2)
+    assert batch.n_beads.min() > 5700
+    params = lh.dpd_params(flow="afbc", seed=13, dim=2, afbc_mode=afbc_mode, **PAPER_2D)
+    a = lh.Micro.from_batch(params, batch)
+    b = lh.Micro.from_batch(params, batch)
+    Lg = torch.from_numpy(batch.L).cuda()
+    st_a = torch.zeros((3, 6), dtype=torch.float64, device="cuda")
+    st_b = torch.zeros_like(st_a)
+    a.advance(Lg, 20, st_a)
+    idx = torch.arange(3, dtype=torch.int32, device="cuda")
+    cnt = torch.tensor([3], dtype=torch.int32, device="cuda")
+    lh.check(lh.lib().lhmm_micro_advance_dev_count(b.h, lh._ptr(Lg), lh._ptr(idx), lh._ptr(cnt), 3,
+                                                   20, lh._ptr(st_b), None, lh._stream_ptr(None)),
+             "lhmm_micro_advance_dev_count")
+    assert a.sync(raise_on_error=False)[0] == b.sync(raise_on_error=False)[0] == lh.OK
+    assert torch.equal(st_a, st_b)
+    for box in range(3):
+        for x, y in zip(a.get_state(box)[:4], b.get_state(box)[:4]):
+            assert np.array_equal(np.asarray(x), np.asarray(y))
+    a.close()
+    b.close()
