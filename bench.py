@@ -315,7 +315,12 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     max_ms = float(t.item())
     bead_steps_rank = batch.total_beads * MICRO_STEPS * args.steps
-    value = bead_steps_rank * world / (max_ms / 1e3)
+    # every rank's batch has its own seed, so the bead counts differ a little:
+    # the job's value is all ranks' bead-steps over the slowest rank's time
+    bs = torch.tensor([float(bead_steps_rank)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(bs, op=dist.ReduceOp.SUM)
+    value = float(bs.item()) / (max_ms / 1e3)
 
     # end to end through the host-buffer entry point (pinned buffers)
     L_pin = torch.from_numpy(batch.L).pin_memory()
@@ -323,11 +328,20 @@ def main():
     micro.advance_host(L_pin.numpy(), MICRO_STEPS, st_pin.numpy())
     e2e_steps = max(2, min(args.steps, 3))
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         micro.advance_host(L_pin.numpy(), MICRO_STEPS, st_pin.numpy())
     e2e_s = time.perf_counter() - t0
-    e2e_val = batch.total_beads * MICRO_STEPS * e2e_steps * world / e2e_s
+    e2e = torch.tensor([e2e_s, float(batch.total_beads * MICRO_STEPS * e2e_steps)],
+                       dtype=torch.float64, device="cuda")
+    if world > 1:  # slowest rank's wall time, all ranks' bead-steps
+        t_max = e2e[:1].clone()
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        dist.all_reduce(e2e, op=dist.ReduceOp.SUM)
+        e2e[0] = t_max[0]
+    e2e_val = float(e2e[1].item()) / float(e2e[0].item())
 
     peaks, src = _peaks()
     clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
