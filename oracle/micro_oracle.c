@@ -428,12 +428,13 @@ int orc_advance(const orc_dpd_params* p, orc_box* b, const double L[9], int n_st
     for (int k = 0; k < 3 * n; ++k) b->vel[k] += hm * b->force[k];
     if (p->flow_mode == ORC_FLOW_AFBC && p->afbc_mode == 1) {
       /* R8 alternative: BC beads keep their velocity about the mean of the BC
-       * beads of their cell (cells of the engine's FP32 width E/n_c). */
+       * beads of their cell; cells are the linked cells of the pair search,
+       * n_c = floor(E / rc) per axis of width exactly E / n_c. */
       int nc[3];
       double wf[3];
       for (int a = 0; a < 3; ++a) {
         nc[a] = (a == 2 && p->dim == 2) ? 1 : (int)floor(b->edge[a] / p->rc);
-        wf[a] = (double)((float)b->edge[a] / (float)nc[a]);
+        wf[a] = b->edge[a] / (double)nc[a];
       }
       const int ncell = nc[0] * nc[1] * nc[2];
       double* sum = (double*)calloc((size_t)ncell * 4, sizeof(double));

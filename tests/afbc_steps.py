@@ -28,7 +28,7 @@ def ambiguous_beads(pos, edge, dim, core_frac, bc_frac, rc=1.0, eps=1e-5):
     for h in (0.5 * core_frac * E, (0.5 * core_frac + bc_frac) * E):
         near |= (np.abs(rp - h) < eps).any(axis=1)
     nc = np.floor(E / rc).astype(int)
-    wf = (E.astype(np.float32) / nc.astype(np.float32)).astype(np.float64)
+    wf = E / nc  # the oracle's cells; the kernel's FP32 width differs by ~1 ulp
     cidx = np.clip(np.floor(x / wf).astype(int), 0, nc - 1)
     frac = x / wf - np.floor(x / wf)
     near |= ((frac < eps) | (frac > 1 - eps)).any(axis=1)

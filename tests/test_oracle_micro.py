@@ -309,7 +309,7 @@ def test_afbc_peculiar_mode_keeps_shell_thermal_and_imposes_cell_means(dim):
     nc = [int(np.floor(e)) for e in edge]
     if dim == 2:
         nc[2] = 1
-    wf = np.array([np.float32(np.float32(e) / np.float32(k)) for e, k in zip(edge, nc)], np.float64)
+    wf = np.array([e / k for e, k in zip(edge, nc)], np.float64)
     ci = np.minimum(np.floor(b1.pos / wf).astype(int), np.array(nc) - 1)
     cell = ci[:, 0] + nc[0] * (ci[:, 1] + nc[1] * ci[:, 2])
     d = (b1.vel - u)[reg == 1]
