@@ -152,6 +152,69 @@ def test_alpha_lambda_scaling_of_output():
     assert np.allclose(outs[1][1], 9.0 * outs[0][1], rtol=1e-13, atol=0)
 
 
+@pytest.mark.parametrize("flow", [O.FLOW_AFBC, O.FLOW_LEES_EDWARDS])
+def test_lambda_star_scales_input_gradient_and_output_stress(flow):
+    # Eq. micro_bc: the box sees lambda* L; Eq. pip: it returns (alpha /
+    # lambda*) <pi'>.  A run with (alpha, lambda*) = (3, 2) under L must equal
+    # 3/2 x a run with (1, 1) under 2 L: doubling is exact in binary floating
+    # point, so both trajectories are the same to the last bit and only the
+    # output factor alpha/lambda* = 1.5 remains.  A dropped, inverted or
+    # doubled lambda* anywhere fails this.
+    L = SHEAR_L if flow == O.FLOW_LEES_EDWARDS else MIXED_L
+    fl = "lees_edwards" if flow == O.FLOW_LEES_EDWARDS else "afbc"
+    runs = []
+    for alpha, lam, Lin in [(3.0, 2.0, L), (1.0, 1.0, 2.0 * L)]:
+        par = O.dpd_params(flow_mode=flow, alpha=alpha, lambda_star=lam)
+        b = _box(6.0, 2, L=2.0 * L, flow=fl)
+        O.compute_forces(par, b, Lin)
+        m, q, err = O.advance(par, b, Lin, 8)
+        assert err == 0
+        runs.append((m, q, b))
+    (m1, q1, b1), (m2, q2, b2) = runs
+    assert np.array_equal(b1.pos, b2.pos) and np.array_equal(b1.vel, b2.vel)
+    assert np.allclose(m1, 1.5 * m2, rtol=1e-15, atol=0)
+    assert np.allclose(q1, 2.25 * q2, rtol=1e-15, atol=0)
+    # and lambda* = 2 is not lambda* = 1: the dynamics do change
+    par = O.dpd_params(flow_mode=flow, alpha=1.0, lambda_star=1.0)
+    b = _box(6.0, 2, L=2.0 * L, flow=fl)
+    O.compute_forces(par, b, L)
+    m3, _, _ = O.advance(par, b, L, 8)
+    assert not np.allclose(m3, m2, rtol=1e-6)
+
+
+def test_3d_kinetic_ik_stress_is_minus_rho_kT():
+    # Eq. kinetic_stress in a periodic box at rest: by equipartition the
+    # kinetic part sum_i m v_i (x) v_i / V has mean rho kBT on the diagonal and
+    # zero off it, for any bead mass (m = 2 here, so a dropped mass factor
+    # fails).  The oracle's kinetic part is its IK sample minus its own pair
+    # virial, -pi V - W (R9: pi = -(K + W)/V).  dt = 0.01 heats a DPD fluid by
+    # about 1 % (reported by the thermostat pin), hence the 1 % floor.
+    par = O.dpd_params(flow_mode=O.FLOW_PERIODIC, mass=2.0)
+    E = 5.0
+    n = int(round(3 * E ** 3))
+    p, v = S.initial_box_state(E, n, 17, 0, mass=par.mass)
+    b = O.Box(E, p, v, n_chains=n // 20, chain_len=10)
+    V = E ** 3
+    O.compute_forces(par, b)
+    O.advance(par, b, ZERO_L, 800)
+    K = []
+    for _ in range(160):
+        O.advance(par, b, ZERO_L, 20)
+        pi6, err = O.ik_sample(par, b)
+        _, W, _ = O.compute_forces(par, b)
+        assert err == 0
+        K.append((-pi6 * V - W) / V)
+    K = np.asarray(K)
+    rho_kT = b.n * par.kBT / V
+    for k in range(6):
+        m, se = _block_se(K[:, k], 16)
+        target = rho_kT if k < 3 else 0.0
+        assert abs(m - target) < max(3 * se, 0.01 * rho_kT), (k, m, se, target)
+    # the kinetic part of one sample is the mass-weighted velocity dyadic
+    vv = par.mass * np.einsum("ia,ib->ab", b.vel, b.vel) / V
+    assert np.allclose(K[-1][[0, 1, 2]], np.diag(vv), rtol=1e-10)
+
+
 def test_split_advance_is_bitwise_resume():
     par = O.dpd_params(flow_mode=O.FLOW_LEES_EDWARDS)
     b1 = _box(5.0, 8, L=SHEAR_L, flow="lees_edwards")
