@@ -10,8 +10,8 @@
  *     the paper names the FDT relation but never prints w^R.
  *  R2 random force: F^R = sigma w^R theta_ij e_ij / sqrt(dt); the 1/sqrt(dt)
  *     of the time-discretised Wiener increment is missing from Eq. random.
- *  R3 theta_ij: Philox4x32-10 (Salmon et al., SC'11) keyed by the box and
- *     counted by (min id, max id, step); Box-Muller on the top 23 bits of
+ *  R3 theta_ij: Philox4x32-10 (Salmon et al., SC'11) keyed by (low seed word,
+ *     high seed word xor box) and counted by (min id, max id, step); Box-Muller on the top 23 bits of
  *     the first two output words, so theta_ij = theta_ji.
  *  R4 FENE: attractive, F_i = -H r_ij / (1 - (r/R0)^2); Eq. fene_force drops
  *     the minus sign that its commented -grad U states.
@@ -80,8 +80,8 @@ double orc_theta_from_words(uint32_t x0, uint32_t x1) {
 
 double orc_pair_theta(uint64_t seed, int box_id, int id_i, int id_j, uint64_t step) {
   uint32_t key[2], ctr[4], out[4];
-  key[0] = (uint32_t)seed ^ (uint32_t)box_id;
-  key[1] = (uint32_t)(seed >> 32);
+  key[0] = (uint32_t)seed;
+  key[1] = (uint32_t)(seed >> 32) ^ (uint32_t)box_id;
   ctr[0] = (uint32_t)(id_i < id_j ? id_i : id_j);
   ctr[1] = (uint32_t)(id_i < id_j ? id_j : id_i);
   ctr[2] = (uint32_t)step;

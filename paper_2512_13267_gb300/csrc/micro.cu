@@ -286,7 +286,9 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
   const float le_inc = vjump * A.dt;             // image offset advance per step
   const unsigned long long step0 = A.state[bid].step;
   const float le0 = A.state[bid].le_offset;
-  const uint32_t k0 = A.seed_lo ^ static_cast<uint32_t>(bid), k1 = A.seed_hi;
+  // key (seed_lo, seed_hi ^ box): distinct (seed, box) pairs with seeds below
+  // 2^32 get distinct keys, so consecutive seeds never share a box's noise
+  const uint32_t k0 = A.seed_lo, k1 = A.seed_hi ^ static_cast<uint32_t>(bid);
   const float hx = 0.5f * sB.len[0], hy = 0.5f * sB.len[1], hz = 0.5f * sB.len[2];
   const unsigned lt_mask = (1u << lane) - 1u;
   unsigned status = 0;

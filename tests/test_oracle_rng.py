@@ -43,6 +43,20 @@ def test_theta_symmetric_and_keyed():
     assert O.pair_theta(2, 3, 5, 9, 17) != base
 
 
+def test_consecutive_seeds_do_not_share_a_box_stream():
+    # R3 keys by (seed_lo, seed_hi ^ box): (seed s, box b) and (s ^ 1, b ^ 1)
+    # must draw different noise (a key of seed_lo ^ box would make them equal)
+    for s in (0, 1, 2, 7, 1000):
+        for b in (0, 1, 5, 1023):
+            for (i, j, step) in [(0, 1, 1), (17, 230, 99)]:
+                assert O.pair_theta(s, b, i, j, step) != O.pair_theta(s ^ 1, b ^ 1, i, j, step)
+    # the documented key and counter layout, through the raw generator
+    seed, box, i, j, step = (5 << 32) | 123, 77, 900, 14, (3 << 32) | 41
+    w = O.philox4x32_10([j, i, step & 0xFFFFFFFF, step >> 32],
+                        [seed & 0xFFFFFFFF, (seed >> 32) ^ box])
+    assert O.pair_theta(seed, box, i, j, step) == O.theta_from_words(w[0], w[1])
+
+
 def test_theta_is_standard_normal():
     th = np.array([O.pair_theta(11, 0, i, i + 1 + (i % 7), 3) for i in range(20000)])
     assert abs(th.mean()) < 4 / np.sqrt(th.size)
