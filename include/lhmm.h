@@ -432,12 +432,19 @@ lhmm_status lhmm_coupled_closure_inputs(lhmm_coupled_t c, float* X_host);
  * process exits.
  *   params     host; n, n_wall, Lx, Ly, h, mass, rho0, c, theta_pb, kernel are
  *              used (the walls are the last n_wall particles).
- *   pos_dev    device, n x 2 float, 8-byte aligned; vel_dev likewise.
+ *   pos_dev    device, n x 2 float, 8-byte aligned; vel_dev likewise.  Positions
+ *              may lie outside [0,Lx) x [0,Ly): each is binned at its periodic
+ *              image, and pair distances are minimum-image distances.
  *   L_out_dev  device, (n - n_wall) x 9 float (the lhmm_micro_advance layout).
  * Returns LHMM_ERR_ARG for n > LHMM_NOALLOC_MAX_PARTICLES or more than
  * LHMM_NOALLOC_MAX_CELLS cells (floor(Lx/h) x floor(Ly/h), at least 3 each).
  * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress).  With lazy module loading (CUDA_MODULE_LOADING=LAZY,
+ * the default of recent CUDA runtimes) that lookup may load the library's
+ * SPH module, and loading a module is when the driver places the array in
+ * device memory.  So make the first call on each device early -- before any
+ * stream capture and before any section in which nothing may allocate;
+ * later calls allocate nothing.
  * Every call uses the same scratch array, so calls that can overlap on the GPU
  * (different streams, or different host threads) race: serialise them.
  * Asynchronous on `stream`. */

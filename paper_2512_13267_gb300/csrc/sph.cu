@@ -61,8 +61,13 @@ __device__ __forceinline__ float2 min_image(float2 a, float2 b, float Lx, float 
   return make_float2(dx, dy);
 }
 
+// Cell of a position, taken at its periodic image in [0, L): positions the
+// caller passes outside the box (the allocation-free entry point takes them
+// as given) bin where their image lies; inside the box the wrap is exact (it
+// subtracts zero), so in-box positions bin as before.
 __device__ __forceinline__ int cell_index(float2 r, const SphArgs& A) {
-  int cx = static_cast<int>(floorf(r.x / A.cwx)), cy = static_cast<int>(floorf(r.y / A.cwy));
+  const float x = r.x - A.Lx * floorf(r.x / A.Lx), y = r.y - A.Ly * floorf(r.y / A.Ly);
+  int cx = static_cast<int>(floorf(x / A.cwx)), cy = static_cast<int>(floorf(y / A.cwy));
   cx = min(max(cx, 0), A.ncx - 1);
   cy = min(max(cy, 0), A.ncy - 1);
   return cx + A.ncx * cy;

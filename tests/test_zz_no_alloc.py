@@ -61,6 +61,43 @@ def test_noalloc_matches_regular_entry_point_on_two_calls():
         ref_h.close()
 
 
+def test_noalloc_bins_positions_outside_the_box_at_their_image():
+    # a caller's positions need not lie in [0, L): every particle shifted by
+    # whole box lengths (up to three in each direction) must give the in-box
+    # result.  Positions on a 2^-16 grid and box lengths 2 and 1 make the
+    # shifts, the wrap and the minimum-image distances exact, so the two calls
+    # agree bit for bit; both must also match the regular entry point.
+    from paper_2512_13267_gb300 import lhmm as lh
+    nx, ny, Lx, Ly = 32, 16, 2.0, 1.0
+    dh = Ly / ny
+    pos = S.sph_lattice(nx, ny, Lx, Ly, seed=5, jitter=0.2)
+    pos = np.round(pos * 65536.0) / 65536.0
+    pos[:, 0] %= Lx
+    pos[:, 1] %= Ly
+    rng = np.random.default_rng(5)
+    vel = rng.normal(scale=0.1, size=pos.shape)
+    k = rng.integers(-3, 4, size=pos.shape)
+    shifted = pos + k * np.array([Lx, Ly])
+    assert np.abs(k).max() == 3 and (shifted < 0).any() and (shifted[:, 0] >= Lx).any()
+    n = pos.shape[0]
+    p = _params(lh, n, 0, Lx, Ly, dh)
+    vel_d = torch.from_numpy(vel.astype(np.float32)).cuda()
+    outs = []
+    for x in (pos, shifted):
+        L = torch.full((n, 9), 7.0, dtype=torch.float32, device="cuda")
+        lh.sph_velgrad_noalloc(p, torch.from_numpy(x.astype(np.float32)).cuda(), vel_d, L)
+        torch.cuda.synchronize()
+        outs.append(L.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+    ref_h = lh.Sph(p, pos.astype(np.float32), vel.astype(np.float32))
+    L_ref = torch.zeros((n, 9), dtype=torch.float32, device="cuda")
+    ref_h.step(0, L_out_dev=L_ref)
+    torch.cuda.synchronize()
+    b = L_ref.cpu().numpy()
+    ref_h.close()
+    assert np.allclose(outs[1], b, rtol=1e-5, atol=1e-6 * np.abs(b).max())
+
+
 def test_noalloc_rejects_oversize_input():
     from paper_2512_13267_gb300 import lhmm as lh
     n = lh.NOALLOC_MAX_PARTICLES + 1
