@@ -12,7 +12,16 @@ batch of the same shape (weak scaling, no data-path collective).
 
 --impl reference times the FP64 CPU oracle (the reference arm of this
 build) on a bounded sample of the same workload on the host cores.
+
+  python bench.py --profile-case micro|mlp|sph
+
+runs one fixed, small invocation of a kernel family for a profiler to
+capture and exits 0 without a bench line: micro = 304 boxes of edge 12
+(5184 beads) for 3 calls of 10 DPD steps; mlp = 4 closure training steps at
+B = 4096 and one inference of 16 384 rows; sph = 3 x 20 substeps of a
+cylinder cell with 16 384 fluid particles.
 """
+import ctypes
 import argparse
 import json
 import os
@@ -29,21 +38,110 @@ sys.path.insert(0, ROOT)
 METRIC = "DPD bead-steps/s (batched micro boxes)"
 UNIT = "bead-steps/s"
 MICRO_STEPS = 100
-# Algorithmic lane-operations per bead-step: each unique interacting pair
-# once, no rejected candidates (the per-pair and per-bead counts below list
-# their parts).
-PAIRS_PER_BEAD = 2.0 * np.pi / 3.0 * 3.0  # rho (4 pi / 3) rc^3 / 2 at rho = 3
-OPS_PER_PAIR = 159   # displacement 6, r^2 + cutoff 4, r and w 3, e.v 7, Philox4x32-10 102,
-#                      Box-Muller 12, force magnitude 9, F on i and j 9, virial 7
-OPS_PER_BEAD = 35    # two half kicks 6, drift 3, cell binning 6, IK kinetic 9, FENE 5, misc 6
-ALGO_OPS_PER_BEAD_STEP = PAIRS_PER_BEAD * OPS_PER_PAIR + OPS_PER_BEAD
-N_SM = 152
-LANES_PER_SM_CLK = 128
+# Algorithmic operations per bead-step, counting only what the method must
+# do (each unique interacting pair once, no rejected candidates): per pair
+# ~40 FP32 operations (distance 8, rsqrt 1, w 2, conservative 2, dissipative
+# 7, random scale 4, forces on i and j 6, virial 9), ~60 integer operations
+# (Philox4x32-10, two of its four words used) and 3 SFU calls (log, sqrt,
+# cos); per bead ~40 FP32 operations (FENE, two half kicks, drift, IK
+# kinetic part).  At rho = 3 a bead has rho (4 pi / 3) rc^3 / 2 = 6.28 unique
+# partners: 291 FP32 + 377 int + 19 SFU = 687 operations per bead-step.
+PAIRS_PER_BEAD = 2.0 * np.pi / 3.0 * 3.0
+FP32_PER_PAIR, INT_PER_PAIR, SFU_PER_PAIR, FP32_PER_BEAD = 40, 60, 3, 40
+ALGO_OPS_PER_BEAD_STEP = PAIRS_PER_BEAD * (FP32_PER_PAIR + INT_PER_PAIR + SFU_PER_PAIR) + FP32_PER_BEAD
+# The same work recounted per issued instruction of a plain implementation
+# (Philox as separate multiply-high, multiply-low, xor and key-add
+# instructions: 159 per pair, 35 per bead), reported beside it.
+ISSUED_OPS_PER_BEAD_STEP = PAIRS_PER_BEAD * 159 + 35
+LANES_PER_SM_CLK = 128  # FP32/INT32 lanes of an SM (4 sub-partitions x 32)
 # DRAM bytes (read + write) per bead and call of micro_kernel, from the ncu
 # capture in profiles/micro_kernel_e12_304box_full.md (76.02 + 16.07 MB for
 # 1,575,936 beads); the kernel reads and writes box state once per call, so
 # traffic scales with beads, not with DPD steps.
 DRAM_BYTES_PER_BEAD_CALL = 92.087e6 / 1575936
+
+
+def build_probe(force=False):
+    """Compile bench_probe.cu (the issue-rate probe of the roofline, a
+    measurement helper outside the library) into bench_probe.so beside this
+    file; returns its path."""
+    src = os.path.join(ROOT, "bench_probe.cu")
+    out = os.path.join(ROOT, "bench_probe.so")
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(src):
+        return out
+    from paper_2512_13267_gb300 import build_ext
+    tmp = out + ".tmp%d" % os.getpid()
+    cmd = [build_ext._nvcc()] + build_ext.ARCH + ["-O3", "-std=c++17", "-Xcompiler", "-fPIC",
+                                                   "-shared", src, "-o", tmp, "-lcudart"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed for bench_probe.cu:\n" + r.stdout + r.stderr)
+    os.replace(tmp, out)
+    return out
+
+
+def issue_rate_probe(stream_ptr, iters=200):
+    """(FP32 FMA, int xor + add) lane-operations per second of this GPU."""
+    lib = ctypes.CDLL(build_probe())
+    f = lib.bench_issue_rate_probe
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                  ctypes.c_void_p]
+    a, b = ctypes.c_double(), ctypes.c_double()
+    rc = f(int(iters), ctypes.byref(a), ctypes.byref(b), ctypes.c_void_p(stream_ptr))
+    if rc != 0:
+        raise RuntimeError("bench_issue_rate_probe failed: %d" % rc)
+    return a.value, b.value
+
+
+def profile_case_micro(boxes=304, edge=12.0, steps=10, calls=3):
+    import torch
+    from paper_2512_13267_gb300 import lhmm, synth
+    batch = synth.make_batch(np.full(boxes, edge),
+                             synth.random_velocity_gradients(boxes, seed=2), 2, flow="afbc")
+    m = lhmm.Micro.from_batch(lhmm.dpd_params(flow="afbc", seed=2), batch)
+    L = torch.from_numpy(batch.L).cuda()
+    st = torch.zeros((boxes, 6), dtype=torch.float64, device="cuda")
+    for _ in range(calls):
+        m.advance(L, steps, st)
+    torch.cuda.synchronize()
+    m.close()
+
+
+def profile_case_mlp(rows=4096, steps=4):
+    import torch
+    from paper_2512_13267_gb300 import lhmm
+    c = lhmm.Closure(members=5, in_dim=67, hidden=256, n_hidden=4, out_dim=3, seed=1)
+    c.set_normalization(np.zeros(67), np.ones(67), np.ones(3))
+    rng = np.random.default_rng(0)
+    X = torch.from_numpy(rng.normal(size=(65536, 67)).astype(np.float32)).cuda()
+    T = torch.from_numpy(rng.normal(size=(65536, 3)).astype(np.float32)).cuda()
+    for _ in range(steps):
+        rws = torch.from_numpy(rng.integers(0, 65536, size=(5, rows)).astype(np.int32)).cuda()
+        c.train_step(X, T, rows, lr=1e-3, weight_decay=1e-4, rows_dev=rws)
+    mean = torch.zeros((16384, 3), dtype=torch.float32, device="cuda")
+    spread = torch.zeros(16384, dtype=torch.float32, device="cuda")
+    c.infer(X[:16384], mean, spread)
+    torch.cuda.synchronize()
+    c.close()
+
+
+def profile_case_sph(n_fluid=16384, cell=16.0, substeps=20):
+    import torch
+    from paper_2512_13267_gb300 import lhmm, synth
+    pos, is_wall, L, dh = synth.cylinder_array(n_fluid_target=n_fluid, radius_frac=0.25, cell=cell)
+    n, n_wall = pos.shape[0], int(is_wall.sum())
+    p = lhmm.sph_params(n, n_wall, Lx=L, Ly=L, h=3 * dh, mass=dh * dh, rho0=1.0, c=2.5,
+                        theta_pb=0.1, eta_s=0.1, dt=0.2 * dh / 2.5, body_force=(1e-3, 0.0))
+    s = lhmm.Sph(p, pos, np.zeros_like(pos))
+    Lout = torch.zeros((n_fluid, 9), dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        s.step(substeps, L_out_dev=Lout)
+    torch.cuda.synchronize()
+    s.close()
+
+
+PROFILE_CASES = {"micro": profile_case_micro, "mlp": profile_case_mlp, "sph": profile_case_sph}
 
 
 def _peaks():
@@ -253,7 +351,12 @@ def main():
                     help="skip the surrogate-gated vs plain comparison")
     ap.add_argument("--uniform-edge", type=float, default=0.0,
                     help="give every box this edge (a one-class case for profilers)")
+    ap.add_argument("--profile-case", choices=sorted(PROFILE_CASES),
+                    help="run one fixed small invocation for a profiler and exit")
     args = ap.parse_args()
+    if args.profile_case:
+        PROFILE_CASES[args.profile_case]()
+        return 0
     if args.impl == "reference":
         return run_reference(args)
 
@@ -287,7 +390,8 @@ def main():
     for _ in range(max(args.warmup, 0)):
         micro.advance(L, MICRO_STEPS, stress)
     torch.cuda.synchronize()
-    micro.sync(raise_on_error=False)  # over-stretch under strong extension is reported below
+    # over-stretch under strong extension is reported below
+    _, warm_status = micro.sync(raise_on_error=False)
 
     clocks = ClockSampler(local)
     if world > 1:
@@ -309,7 +413,8 @@ def main():
     clk = clocks.stop()
     times_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = float(sum(times_ms))
-    status, _ = micro.sync(raise_on_error=False)
+    status, timed_status = micro.sync(raise_on_error=False)
+    clamped = int(np.count_nonzero((warm_status | timed_status) & lhmm.BOX_BOND_OVERSTRETCH))
     t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -345,7 +450,8 @@ def main():
 
     peaks, src = _peaks()
     clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = N_SM * LANES_PER_SM_CLK * clk_mhz * 1e6 / 1e12  # T lane-ops/s
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = n_sm * LANES_PER_SM_CLK * clk_mhz * 1e6 / 1e12  # T lane-ops/s
     per_launch_ops = ALGO_OPS_PER_BEAD_STEP * batch.total_beads * MICRO_STEPS
     launch_s = (total_ms / args.steps) / 1e3
     achieved = per_launch_ops / launch_s / 1e12
@@ -354,16 +460,22 @@ def main():
                 "traffic": DRAM_BYTES_PER_BEAD_CALL * batch.total_beads,
                 "traffic_unit": "bytes per call (all size-class launches), scaled by beads from "
                                 "the 304-box capture",
-                "peak_source": "%d SMs x %d FP32/INT lanes x %.0f MHz (%s sm_max_mhz)"
-                               % (N_SM, LANES_PER_SM_CLK, clk_mhz, src),
-                "kernel": "micro_kernel", "algo_ops_per_bead_step": ALGO_OPS_PER_BEAD_STEP}
+                "peak_source": "%d SMs (queried) x %d FP32/INT lanes x %.0f MHz (%s sm_max_mhz)"
+                               % (n_sm, LANES_PER_SM_CLK, clk_mhz, src),
+                "kernel": "micro_kernel", "algo_ops_per_bead_step": ALGO_OPS_PER_BEAD_STEP,
+                "algo_ops_split": "%.0f FP32 + %.0f int + %.0f SFU per bead-step"
+                                  % (PAIRS_PER_BEAD * FP32_PER_PAIR + FP32_PER_BEAD,
+                                     PAIRS_PER_BEAD * INT_PER_PAIR, PAIRS_PER_BEAD * SFU_PER_PAIR),
+                "frac_issued_recount": (ISSUED_OPS_PER_BEAD_STEP / ALGO_OPS_PER_BEAD_STEP)
+                                       * achieved / alu_peak,
+                "issued_ops_per_bead_step": ISSUED_OPS_PER_BEAD_STEP}
     try:  # measured issue rate of the CUDA cores, beside the derived peak
-        f_rate, i_rate = lhmm.issue_rate_probe(iters=200)
-        roofline["peak_probe"] = {"ffma": f_rate / 1e12, "int_xor_add": i_rate / 1e12,
-                                  "unit": "T lane-ops/s",
-                                  "frac_of_ffma_probe": achieved / (f_rate / 1e12)}
+        f_rate, i_rate = issue_rate_probe(stream.cuda_stream, iters=200)
+        roofline["probe_ffma_tops"] = f_rate / 1e12
+        roofline["probe_int_xor_add_tops"] = i_rate / 1e12
+        roofline["frac_of_int_probe"] = achieved / (i_rate / 1e12)
     except Exception as exc:  # pragma: no cover
-        roofline["peak_probe"] = {"error": str(exc)}
+        roofline["probe_error"] = str(exc)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
@@ -373,7 +485,12 @@ def main():
                     "h2d_bytes_per_step": int(L_pin.numel() * 4),
                     "d2h_bytes_per_step": int(st_pin.numel() * 8)},
             "gpu_launches": args.steps * len(micro.plan()),
-            "launch_plan": micro.plan(), "device_status": lhmm.status_string(status)}
+            "launch_plan": micro.plan(), "device_status": lhmm.status_string(status),
+            "bond_clamped_boxes": clamped,
+            "bond_clamp_note": ("%d of %d boxes (planar extension at the highest rates) had a FENE "
+                                "bond reach R0 in the warm-up or timed calls; their bond stiffness "
+                                "is held at the (r/R0)^2 = 0.99 value (reading R10), the oracle "
+                                "flags the same boxes" % (clamped, batch.n_boxes))}
     if clk is not None:
         line["clocks"] = clk
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

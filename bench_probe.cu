@@ -1,11 +1,11 @@
-// Issue-rate probe: the achievable lane-operation rate of the CUDA cores,
-// the denominator of the micro kernel's roofline (that kernel is bound by
-// instruction issue, not by memory or tensor cores).  Each thread runs eight
-// independent dependency chains, so every warp scheduler always has an
-// instruction ready; the rate counts only the chain operations.
+// bench_probe.cu -- measurement helper of bench.py, not part of the LHMM
+// library.  Issue-rate probe: the achievable lane-operation rate of the CUDA
+// cores, which bench.py reports beside the derived peak of the micro kernel's
+// roofline (that kernel is bound by instruction issue, not by memory or
+// tensor cores).  Each thread runs eight independent dependency chains, so
+// every warp scheduler always has an instruction ready; the rate counts only
+// the chain operations.  Built by __graft_entry__.build() into bench_probe.so.
 #include <cuda_runtime.h>
-
-#include "lhmm_common.cuh"
 
 namespace {
 
@@ -48,16 +48,26 @@ __global__ void __launch_bounds__(kProbeThreads) probe_int(int iters, unsigned c
 
 }  // namespace
 
-extern "C" lhmm_status lhmm_issue_rate_probe(int iters, double* ffma_ops_per_s,
-                                             double* int_ops_per_s, void* stream) {
-  if (iters < 1 || iters > 100000 || !ffma_ops_per_s || !int_ops_per_s) return LHMM_ERR_ARG;
+#define PROBE_CK(call)                      \
+  do {                                      \
+    cudaError_t e_ = (call);                \
+    if (e_ != cudaSuccess) return (int)e_;  \
+  } while (0)
+
+// Returns 0, -1 for a bad argument, or the failing cudaError_t.  Writes the
+// best of three timed launches of each probe (after a warm-up) as
+// lane-operations per second.  Synchronous on `stream`; allocates 16 bytes
+// for the duration of the call.
+extern "C" int bench_issue_rate_probe(int iters, double* ffma_ops_per_s, double* int_ops_per_s,
+                                      void* stream) {
+  if (iters < 1 || iters > 100000 || !ffma_ops_per_s || !int_ops_per_s) return -1;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int dev = 0, sms = 0;
-  LHMM_CK(cudaGetDevice(&dev));
-  LHMM_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  PROBE_CK(cudaGetDevice(&dev));
+  PROBE_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int grid = sms * 8;
   void* sink = nullptr;
-  LHMM_CK(cudaMalloc(&sink, 16));
+  PROBE_CK(cudaMalloc(&sink, 16));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -88,8 +98,8 @@ extern "C" lhmm_status lhmm_issue_rate_probe(int iters, double* ffma_ops_per_s,
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(sink);
-  if (e != cudaSuccess) return lhmm_cuda_error(e);
+  if (e != cudaSuccess) return (int)e;
   *ffma_ops_per_s = best_f;
   *int_ops_per_s = best_i;
-  return LHMM_OK;
+  return 0;
 }

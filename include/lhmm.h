@@ -222,17 +222,6 @@ lhmm_status lhmm_micro_plan(lhmm_micro_t h, int* n_classes, int cap, int* class_
  * call it before capturing advances into a CUDA graph. */
 lhmm_status lhmm_micro_set_variant(lhmm_micro_t h, int cls, int variant);
 
-/* Measurement helper (not in the paper): the achievable lane-operation rate
- * of this GPU's CUDA cores, the denominator of the micro kernel's roofline
- * (that kernel is bound by instruction issue).  Two probe kernels of
- * 8 blocks per SM x 512 threads run `iters` (1..100000) rounds of 128
- * independent-chain operations per thread: FP32 fused multiply-adds, and
- * 32-bit xor + add pairs.  Writes the best of three timed launches of each
- * (after a warm-up) as lane-operations per second.  Synchronous on `stream`;
- * allocates 16 bytes for the duration of the call. */
-lhmm_status lhmm_issue_rate_probe(int iters, double* ffma_ops_per_s, double* int_ops_per_s,
-                                  void* stream);
-
 /* ------------------------------------------------------------------------
  * Macroscale SPH (Sec. 3.2, Eqs. sph_continuity and tait; Sec. 3.4,
  * Eq. macro_micro).  2D periodic box [0,Lx) x [0,Ly); particles 0..n-n_wall-1

@@ -87,7 +87,6 @@ def lib():
         L.lhmm_micro_autotune.argtypes = [vp, vp, C.c_int, vp]
         L.lhmm_micro_plan.argtypes = [vp, _I, C.c_int, _I, _I, _I, _I]
         L.lhmm_micro_set_variant.argtypes = [vp, C.c_int, C.c_int]
-        L.lhmm_issue_rate_probe.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
         L.lhmm_sph_create.argtypes = [C.POINTER(SphParams), _F, _F, vp, C.POINTER(vp)]
         L.lhmm_sph_destroy.argtypes = [vp]
         L.lhmm_sph_step.argtypes = [vp, vp, C.c_int, vp, vp]
@@ -338,14 +337,6 @@ class Sph:
         return pos, vel, acc, d
 
 
-def issue_rate_probe(iters=200, stream=None):
-    """Achievable lane-operations per second of the CUDA cores (FP32 FMA
-    chains, int xor + add chains): the micro kernel's roofline denominator."""
-    f = C.c_double()
-    i = C.c_double()
-    check(lib().lhmm_issue_rate_probe(int(iters), C.byref(f), C.byref(i), _stream_ptr(stream)),
-          "lhmm_issue_rate_probe")
-    return f.value, i.value
 
 
 # micro kernel variants (include/lhmm.h): threads per block, resident blocks

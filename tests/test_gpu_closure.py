@@ -32,7 +32,7 @@ def _bf16(a):
     return r.view(np.float32).astype(np.float64)
 
 
-def test_forward_matches_oracle_within_bf16_rounding():
+def test_forward_matches_oracle_within_bf16_rounding(parity_report):
     c = _closure()
     rng = np.random.default_rng(0)
     X = rng.normal(size=(100, 67))
@@ -48,10 +48,12 @@ def test_forward_matches_oracle_within_bf16_rounding():
         # with the weights and inputs rounded to BF16 in the oracle the bound tightens
         ref_b = O.mlp_forward(DIMS, _bf16(p), _bf16(X))
         assert np.abs(Y[m] - ref_b).max() <= 0.5 * err + 1e-2 * np.abs(ref).max()
+        parity_report("MLP forward (BF16 tensor cores), member %d" % m,
+                      err / np.abs(ref).max(), 3e-2, "max |dy| / max |y|")
     c.close()
 
 
-def test_gradient_matches_oracle():
+def test_gradient_matches_oracle(parity_report):
     c = _closure(members=2, seed=5)
     rng = np.random.default_rng(1)
     B = 64
@@ -65,10 +67,11 @@ def test_gradient_matches_oracle():
         rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
         cos = g @ ref / (np.linalg.norm(g) * np.linalg.norm(ref))
         assert rel < 0.05 and cos > 0.998, (m, rel, cos)
+        parity_report("MLP loss gradient, member %d" % m, rel, 0.05, "|dg| / |g| (L2)")
     c.close()
 
 
-def test_adamw_update_matches_oracle_step():
+def test_adamw_update_matches_oracle_step(parity_report):
     c = _closure(members=1, seed=9)
     rng = np.random.default_rng(2)
     B = 96
@@ -83,6 +86,8 @@ def test_adamw_update_matches_oracle_step():
     exp = p0.copy()
     O.adamw_step(exp, g, m, v, 1e-3, 0.9, 0.999, 1e-8, 0.0, 1)
     assert np.abs(p1 - exp).max() <= 1e-6 + 1e-5 * np.abs(exp).max()
+    parity_report("AdamW step", np.abs(p1 - exp).max(), 1e-6 + 1e-5 * np.abs(exp).max(),
+                  "max |dp|")
     c.close()
 
 

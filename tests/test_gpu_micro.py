@@ -53,18 +53,25 @@ def _minimage(d, E):
     return d - E * np.rint(d / E)
 
 
-@pytest.mark.parametrize("flow", ["afbc", "periodic", "lees_edwards"])
-def test_initial_forces_match_oracle(flow):
+@pytest.mark.parametrize("flow,lam", [("afbc", 1.0), ("periodic", 1.0), ("lees_edwards", 1.0),
+                                      ("afbc", 2.0), ("lees_edwards", 2.0)])
+def test_initial_forces_match_oracle(flow, lam, parity_report):
+    # lam = lambda*: the boxes see lambda* L (Eq. micro_bc); under Lees-Edwards
+    # the sliding images' velocity jump, under AFBC the streaming velocity of
+    # the dissipative force's reference, both scale with it
     batch = _ragged_afbc_batch()
     if flow == "lees_edwards":
         batch.L[:] = 0.0
         batch.L[:, 1] = 0.4
-    m, op, boxes = _pair(batch, flow, seed=3)
+    m, op, boxes = _pair(batch, flow, seed=3, lambda_star=lam)
+    worst = 0.0
     for b, ob in enumerate(boxes):
         pos, vel, f, step, _ = m.get_state(b)
         assert step == 0
         assert np.abs(f - ob.force).max() <= 1e-4, (b, np.abs(f - ob.force).max())
         assert np.abs(_minimage(pos - ob.pos, batch.edges[b][0])).max() < 1e-5
+        worst = max(worst, np.abs(f - ob.force).max())
+    parity_report("initial forces, %s, lambda*=%g" % (flow, lam), worst, 1e-4, "max |dF|")
     m.close()
 
 
@@ -87,32 +94,52 @@ def test_config0_single_box_forces_and_one_step_stress():
     m.close()
 
 
-@pytest.mark.parametrize("flow", ["afbc", "lees_edwards", "periodic"])
-def test_fifty_step_trajectory(flow):
+@pytest.mark.parametrize("flow,lam,alpha", [("afbc", 1.0, 1.0), ("lees_edwards", 1.0, 1.0),
+                                            ("periodic", 1.0, 1.0), ("afbc", 2.0, 3.0),
+                                            ("lees_edwards", 2.0, 3.0)])
+def test_fifty_step_trajectory(flow, lam, alpha, parity_report):
+    # positions after 50 steps within 1e-3; the 50-step averages of the IK
+    # stress (Eq. pip: scaled by alpha/lambda*) within 3 standard errors of
+    # the oracle's, the SE taken from the oracle's own per-step samples
+    # (stress_sq - stress^2 over 50 samples; consecutive samples are
+    # correlated, so this SE is small and the bound strict); the second
+    # moments stress_sq within 2 % of their scale
     batch = _ragged_afbc_batch(seed=8)
     if flow == "lees_edwards":
         batch.L[:] = 0.0
         batch.L[:, 1] = 0.5
-    m, op, boxes = _pair(batch, flow, seed=9)
+    m, op, boxes = _pair(batch, flow, seed=9, lambda_star=lam, alpha=alpha)
     L = torch.from_numpy(batch.L).cuda()
     st = torch.zeros((batch.n_boxes, 6), dtype=torch.float64, device="cuda")
-    m.advance(L, 50, st)
+    sq = torch.zeros((batch.n_boxes, 6), dtype=torch.float64, device="cuda")
+    m.advance(L, 50, st, stress_sq_dev=sq)
     m.sync()
-    got = st.cpu().numpy()
+    got, got_sq = st.cpu().numpy(), sq.cpu().numpy()
+    w_pos, w_se, w_sq = 0.0, 0.0, 0.0
     for b, ob in enumerate(boxes):
-        ref, _, err = O.advance(op, ob, batch.L[b], 50)
+        ref, ref_sq, err = O.advance(op, ob, batch.L[b], 50)
         assert err == 0
         pos, vel, f, step, _ = m.get_state(b)
         assert step == 50
         dpos = np.abs(_minimage(pos - ob.pos, batch.edges[b][0])).max()
         assert dpos <= 1e-3, (b, dpos)
-        # 50-step average of the IK stress: FP32 trajectory vs FP64 trajectory
-        scale = 1.0 + np.abs(ref).max()
-        assert np.abs(got[b] - ref).max() <= 2e-2 * scale, (b, got[b], ref)
+        se = np.sqrt(np.maximum(ref_sq - ref * ref, 0.0) / 50)
+        d = np.abs(got[b] - ref)
+        # boxes of edge 3 have an empty AFBC core (zero stress, zero SE)
+        assert np.all(d <= 3 * se + 1e-12 * (1 + np.abs(ref))), (b, got[b], ref, se)
+        dq = np.abs(got_sq[b] - ref_sq).max()
+        assert dq <= 2e-2 * (1.0 + np.abs(ref_sq).max()), (b, got_sq[b], ref_sq)
+        w_pos = max(w_pos, dpos)
+        w_se = max(w_se, float(np.max(np.where(se > 0, d / np.where(se > 0, se, 1), 0))))
+        w_sq = max(w_sq, dq / (1.0 + np.abs(ref_sq).max()))
+    tag = "%s, lambda*=%g, alpha=%g" % (flow, lam, alpha)
+    parity_report("50-step positions, " + tag, w_pos, 1e-3, "max |dr|")
+    parity_report("50-step stress average, " + tag, w_se, 3.0, "max |dpi| / SE")
+    parity_report("50-step stress second moment, " + tag, w_sq, 2e-2, "max |dq| / (1 + max|q|)")
     m.close()
 
 
-def test_block_averaged_stress_config0():
+def test_block_averaged_stress_config0(parity_report):
     # 2000 steps of the single 10^3 box under Lees-Edwards shear 0.1: block
     # averages over 100-step calls, GPU vs oracle within 3 combined SEs
     batch = S.single_shear_box(seed=1)
@@ -131,6 +158,8 @@ def test_block_averaged_stress_config0():
     se = np.sqrt(g.var(axis=0, ddof=1) / len(g) + o.var(axis=0, ddof=1) / len(o))
     diff = np.abs(g.mean(axis=0) - o.mean(axis=0))
     assert np.all(diff <= 3 * se + 1e-6), (g.mean(0), o.mean(0), se)
+    parity_report("2000-step block-averaged stress, 10^3 box, LE 0.1", float(np.max(diff / se)),
+                  3.0, "max |dpi| / combined block SE")
     # eta_p = pi_xy / gdot and N1 = pi_xx - pi_yy are positive under shear
     assert g.mean(axis=0)[3] > 0
     m.close()
@@ -365,29 +394,38 @@ def test_bonded_pairs_excluded_matches_oracle():
     m.close()
 
 
-def test_afbc_peculiar_mode_matches_oracle():
+def test_afbc_peculiar_mode_matches_oracle(parity_report):
     # afbc_mode = 1: BC beads keep their velocity about their cell's BC mean;
-    # a 50-step trajectory and, restarted from the GPU state, each step's update
-    from afbc_steps import stepwise_afbc_parity
+    # the first step and, restarted from the GPU state, each later step's
+    # update (beads whose region or cell the two precisions may choose
+    # differently are left out and counted)
+    from afbc_steps import ambiguous_beads, stepwise_afbc_parity
     batch = _ragged_afbc_batch(seed=21)
     m, op, boxes = _pair(batch, "afbc", seed=21, afbc_mode=1)
     L = torch.from_numpy(batch.L).cuda()
     st = torch.zeros((batch.n_boxes, 6), dtype=torch.float64, device="cuda")
     m.advance(L, 1, st)
     m.sync()
+    skipped = 0
     for b, ob in enumerate(boxes):
         O.advance(op, ob, batch.L[b], 1)
         _, vel, _, _, _ = m.get_state(b)
-        assert np.abs(vel - ob.vel).max() <= 1e-4, (b, np.abs(vel - ob.vel).max())
-    assert stepwise_afbc_parity(m, op, batch, 30) <= 10
+        amb = ambiguous_beads(ob.pos, batch.edges[b], 3, op.core_frac, op.bc_frac)
+        ok = np.abs(vel - ob.vel).max(axis=1) <= 1e-4
+        assert np.all(ok | amb), (b, np.abs(vel - ob.vel).max())
+        skipped += int(np.count_nonzero(amb & ~ok))
+    skipped += stepwise_afbc_parity(m, op, batch, 30)
+    assert skipped <= 10
+    parity_report("thermal-shell AFBC one-step map, 31 steps x 7 boxes, 3D", skipped, 10,
+                  "bead velocities left out as ambiguous")
     m.close()
 
 
 def test_issue_rate_probe_is_near_the_lane_count_times_clock():
-    # the roofline denominator: 152 SMs x 128 lanes x clock (at most ~2.07 GHz)
-    lh = _lh()
-    f, i = lh.issue_rate_probe(iters=50)
-    nominal = 152 * 128 * 2.07e9
+    # bench.py's roofline denominator: SMs x 128 lanes x clock (<= ~2.07 GHz)
+    import bench
+    f, i = bench.issue_rate_probe(torch.cuda.current_stream().cuda_stream, iters=50)
+    nominal = torch.cuda.get_device_properties(0).multi_processor_count * 128 * 2.07e9
     assert 0.3 * nominal < f < 1.05 * nominal, f
     assert 0.3 * nominal < i < 1.05 * nominal, i
 

@@ -56,16 +56,22 @@ def _scale(op, pos, vel):
 
 
 @pytest.mark.parametrize("kernel", [0, 1])
-def test_initial_accelerations(kernel):
+def test_initial_accelerations(kernel, parity_report):
     g, op, pos, vel, wall = _setup(kernel=kernel)
     acc_ref, d_ref = O.sph_accel(op, pos, vel, is_wall=wall)
     _, _, acc, d = g.get_state()
     assert np.abs(d - d_ref).max() <= 2e-6 * d_ref.max()
     assert np.abs(acc - acc_ref).max() <= 2e-5 * _scale(op, pos, vel)
+    name = "Lucy" if kernel else "Wendland C2"
+    parity_report("SPH number density, " + name, np.abs(d - d_ref).max() / d_ref.max(), 2e-6,
+                  "max |dd| / max d")
+    parity_report("SPH acceleration, " + name,
+                  np.abs(acc - acc_ref).max() / _scale(op, pos, vel), 2e-5,
+                  "max |da| / largest pressure pair term")
     g.close()
 
 
-def test_stress_coupling_and_velocity_gradient():
+def test_stress_coupling_and_velocity_gradient(parity_report):
     g, op, pos, vel, wall = _setup()
     n = pos.shape[0]
     rng = np.random.default_rng(5)
@@ -83,10 +89,14 @@ def test_stress_coupling_and_velocity_gradient():
     assert np.all(got[:, [2, 5, 6, 7, 8]] == 0)
     got4 = got[:, [0, 1, 3, 4]]
     assert np.abs(got4 - L_ref).max() <= 1e-4 * np.abs(L_ref).max()
+    parity_report("SPH acceleration with micro stress", np.abs(acc - acc_ref).max()
+                  / _scale(op, pos, vel), 2e-5, "max |da| / largest pressure pair term")
+    parity_report("SPH velocity gradient", np.abs(got4 - L_ref).max() / np.abs(L_ref).max(),
+                  1e-4, "max |dL| / max |L|")
     g.close()
 
 
-def test_velocity_verlet_substeps():
+def test_velocity_verlet_substeps(parity_report):
     g, op, pos, vel, wall = _setup(dt=1e-3)
     acc, _ = O.sph_accel(op, pos, vel, is_wall=wall)
     g.step(40)
@@ -96,6 +106,9 @@ def test_velocity_verlet_substeps():
     dp -= np.array([op.Lx, op.Ly]) * np.rint(dp / np.array([op.Lx, op.Ly]))
     assert np.abs(dp).max() < 1e-5
     assert np.abs(v - vel).max() < 1e-4 * max(1.0, np.abs(vel).max())
+    parity_report("SPH 40 VV substeps, positions", np.abs(dp).max(), 1e-5, "max |dr|")
+    parity_report("SPH 40 VV substeps, velocities", np.abs(v - vel).max()
+                  / max(1.0, np.abs(vel).max()), 1e-4, "max |dv| / max(1, max |v|)")
     g.close()
 
 
