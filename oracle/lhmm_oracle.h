@@ -97,6 +97,15 @@ int orc_advance_batch(const orc_dpd_params* p, orc_box* boxes, int n_boxes,
                       int n_threads, int* status /* n_boxes */);
 /* one IK sample (no time average, no alpha scaling) from the current state */
 int orc_ik_sample(const orc_dpd_params* p, orc_box* b, const double L[9], double pi6[6]);
+
+/* Momentum and energy of one box (Eq. motion's conserved quantities): out =
+ * [P_x, P_y, P_z, kinetic sum m v^2 / 2, conservative DPD potential (every
+ * non-excluded pair once, U = a rc/2 (1 - r/rc)^2 for r < rc), FENE potential
+ * (every bond, U = -H R0^2/2 ln(1 - r^2/R0^2)), total of the three energies,
+ * 0].  Brute force over all pairs, minimum images as the forces take them.
+ * Returns ORC_ERR_BOND_OVERSTRETCH for a bond at |r| >= R0 (its energy is
+ * then taken at (r/R0)^2 = 0.99, reading R10). */
+int orc_diagnostics(const orc_dpd_params* p, const orc_box* b, const double L[9], double out[8]);
 /* AFBC region of a position: 0 core, 1 BC shell, 2 buffer */
 int orc_afbc_region(const orc_dpd_params* p, const double edge[3], const double r[3]);
 /* length fraction of the segment a->b inside the centred box |x_k| < half[k] */

@@ -398,6 +398,49 @@ int orc_ik_sample(const orc_dpd_params* p, orc_box* b, const double L[9], double
   return err;
 }
 
+/* Conserved quantities of Eq. motion without dissipation: total momentum,
+ * kinetic energy and the potentials whose negative gradients are the
+ * conservative force (Eq. conservative: a (1 - r/rc) = -d/dr [a rc/2
+ * (1 - r/rc)^2]) and the FENE force (Eq. fene_force, R4: -H r/(1 - r^2/R0^2)
+ * = -d/dr [-H R0^2/2 ln(1 - r^2/R0^2)]). */
+int orc_diagnostics(const orc_dpd_params* p, const orc_box* b, const double L[9], double out[8]) {
+  const double gdot = lees_edwards_rate(p, L);
+  int err = 0;
+  double P[3] = {0, 0, 0}, kin = 0.0, uc = 0.0, uf = 0.0;
+  for (int i = 0; i < b->n; ++i) {
+    double v2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      P[a] += p->mass * b->vel[3 * i + a];
+      v2 += b->vel[3 * i + a] * b->vel[3 * i + a];
+    }
+    kin += 0.5 * p->mass * v2;
+  }
+  orc_box* bb = (orc_box*)b; /* pair_disp reads only */
+  for (int i = 0; i < b->n; ++i) {
+    for (int j = i + 1; j < b->n; ++j) {
+      double dr[3], dv[3];
+      pair_disp(p, bb, gdot, i, j, dr, dv);
+      const double r = sqrt(dr[0] * dr[0] + dr[1] * dr[1] + dr[2] * dr[2]);
+      if (r < p->rc && !excluded(p, bb, i, j)) {
+        const double w = 1.0 - r / p->rc;
+        uc += 0.5 * p->a_ij * p->rc * w * w;
+      }
+    }
+  }
+  const int np = b->n_chains * b->chain_len;
+  for (int i = 0; i + 1 < np; ++i) {
+    if ((i + 1) % b->chain_len == 0) continue; /* chain end */
+    double dr[3], dv[3];
+    pair_disp(p, bb, gdot, i, i + 1, dr, dv);
+    double x = (dr[0] * dr[0] + dr[1] * dr[1] + dr[2] * dr[2]) / (p->R0 * p->R0);
+    if (!(x < 1.0)) { x = 0.99; err |= ORC_ERR_BOND_OVERSTRETCH; }
+    uf += -0.5 * p->H_fene * p->R0 * p->R0 * log(1.0 - x);
+  }
+  out[0] = P[0]; out[1] = P[1]; out[2] = P[2];
+  out[3] = kin; out[4] = uc; out[5] = uf; out[6] = kin + uc + uf; out[7] = 0.0;
+  return err;
+}
+
 /* velocity-Verlet steps (R6) with the imposed flow (R7, R8) and an IK sample
  * after each full step; time average over the call (Eq. kinetic_stress,
  * N'_t = n_steps) scaled by alpha/lambda* (Eq. pip). */

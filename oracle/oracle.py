@@ -73,6 +73,7 @@ def lib():
         L.orc_advance_batch.argtypes = [C.POINTER(DpdParams), C.POINTER(_Box), C.c_int, _D,
                                         C.c_int, _D, _D, C.c_int, _I]
         L.orc_ik_sample.argtypes = [C.POINTER(DpdParams), C.POINTER(_Box), _D, _D]
+        L.orc_diagnostics.argtypes = [C.POINTER(DpdParams), C.POINTER(_Box), _D, _D]
         L.orc_afbc_region.argtypes = [C.POINTER(DpdParams), _D, _D]
         L.orc_segment_fraction.argtypes = [_D, _D, _D]
         L.orc_segment_fraction.restype = C.c_double
@@ -205,6 +206,15 @@ def ik_sample(p, box, L=None):
     pi6 = np.zeros(6)
     err = lib().orc_ik_sample(C.byref(p), C.byref(box.s), _dp(L), _dp(pi6))
     return pi6, err
+
+
+def diagnostics(p, box, L=None):
+    """[P_x, P_y, P_z, kinetic, conservative DPD potential, FENE potential,
+    total energy, 0] of one box, and the error bits."""
+    L = _L(np.zeros(9) if L is None else L)
+    out = np.zeros(8)
+    err = lib().orc_diagnostics(C.byref(p), C.byref(box.s), _dp(L), _dp(out))
+    return out, err
 
 
 def afbc_region(p, edge, r):

@@ -382,3 +382,46 @@ def test_afbc_peculiar_mode_keeps_shell_thermal_and_imposes_cell_means(dim):
     moving = 3 if dim == 3 else 2
     assert d[:, :moving].var() > 0.3  # thermal, not frozen
     assert np.abs((b0.vel - u)[reg == 1]).max() < 1e-12  # mode 0: exact overwrite
+
+
+def test_diagnostic_potentials_closed_forms():
+    # two solvent beads at r = 0.4: U = a rc/2 (1 - r/rc)^2 = 12.5 * 0.36;
+    # a 2-bead chain at r = 0.9 adds the FENE energy -H R0^2/2 ln(1 - r^2/R0^2)
+    par = O.dpd_params(flow_mode=O.FLOW_PERIODIC)
+    x = np.array([[1.0, 2.0, 2.0], [1.4, 2.0, 2.0]])
+    v = np.array([[0.5, -1.0, 0.0], [0.1, 0.2, 0.3]])
+    out, err = O.diagnostics(par, O.Box(5.0, x, v, n_chains=0, chain_len=2))
+    assert err == 0
+    assert np.allclose(out[:3], [0.6, -0.8, 0.3], rtol=0, atol=1e-15)
+    assert abs(out[3] - 0.5 * (1.25 + 0.14)) < 1e-15
+    assert abs(out[4] - 4.5) < 1e-13 and out[5] == 0.0
+    x = np.array([[4.6, 2.0, 2.0], [0.5, 2.0, 2.0]])  # 0.9 apart through the x boundary
+    out, err = O.diagnostics(par, O.Box(5.0, x, np.zeros((2, 3)), n_chains=1, chain_len=2))
+    assert abs(out[4] - 12.5 * 0.01) < 1e-12
+    assert abs(out[5] + 0.5 * 30.0 * 2.25 * np.log(1 - 0.81 / 2.25)) < 1e-12
+    assert abs(out[6] - out[3] - out[4] - out[5]) < 1e-12
+
+
+def test_energy_conserved_without_thermostat_to_second_order_in_dt():
+    # gamma = sigma = 0: Eq. motion is Hamiltonian with the potentials of the
+    # diagnostic, so velocity-Verlet keeps the total energy up to an O(dt^2)
+    # error that does not drift.  The forces and the potentials are written
+    # separately; a sign or factor mistake in either breaks this.
+    errs = []
+    for dt in (0.004, 0.002):
+        par = O.dpd_params(flow_mode=O.FLOW_PERIODIC, gamma=0.0, sigma=0.0, dt=dt)
+        b = _box(4.0, 23)
+        O.compute_forces(par, b)
+        d0 = O.diagnostics(par, b)[0]
+        e0 = d0[6]
+        dev = []
+        for _ in range(20):
+            O.advance(par, b, ZERO_L, int(round(0.02 / dt)))
+            d, err = O.diagnostics(par, b)
+            assert err == 0
+            dev.append(d[6] - e0)
+        errs.append(np.abs(dev).max())
+        assert np.abs(O.diagnostics(par, b)[0][:3] - d0[:3]).max() < 1e-10  # momentum kept
+    # halving dt quarters the energy error (2nd order), within 30 %
+    assert 2.8 < errs[0] / errs[1] < 5.2, errs
+    assert errs[0] < 2e-3 * b.n
