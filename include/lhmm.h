@@ -156,6 +156,23 @@ lhmm_status lhmm_micro_advance_dev_count(lhmm_micro_t h, const float* L_dev,
                                          int max_active, int n_steps, double* stress_dev,
                                          double* stress_sq_dev, void* stream);
 
+/* FP64 momentum and energy of every box of the current state (Eq. motion:
+ * without its dissipative and random terms the dynamics conserve the total
+ * momentum and the energy below; with them the momentum is still conserved).
+ *   diag_dev  device, n_boxes x 8 double, row b = [P_x, P_y, P_z,
+ *             kinetic energy sum m v^2/2, conservative DPD potential
+ *             sum over non-excluded pairs within rc of a rc/2 (1 - r/rc)^2
+ *             (the potential of Eq. conservative), FENE potential sum over
+ *             bonds of -H R0^2/2 ln(1 - r^2/R0^2) (Eq. fene_force),
+ *             total energy (the sum of the three), 1 if a bond was at
+ *             |r| >= R0 (its energy then taken at (r/R0)^2 = 0.99) else 0].
+ * Sums are accumulated in FP64 from the FP32 state; pairs by brute force
+ * over each box with minimum images (Lees-Edwards shifted across y), so the
+ * cost is O(N^2) per box: a diagnostic, not a per-step call.  Velocities are
+ * lab-frame (the imposed flow is not subtracted).  Asynchronous on `stream`;
+ * reads the state the last advance left. */
+lhmm_status lhmm_micro_diagnostics(lhmm_micro_t h, double* diag_dev, void* stream);
+
 /* The same over host buffers: copies L_host (n_boxes x 9) in, advances all
  * boxes, copies stress (n_boxes x 6) and optionally stress_sq back, and waits
  * for the stream.  Synchronous.  Uses staging buffers owned by the handle. */

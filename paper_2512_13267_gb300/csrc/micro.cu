@@ -888,6 +888,122 @@ __global__ void __launch_bounds__(T, MINB) micro_kernel_persistent(const MicroAr
   }
 }
 
+// ---------------------------------------------------------------------------
+// Conserved-quantity diagnostics (Eq. motion without its dissipative and
+// random terms conserves momentum and the energy below).  One block per box
+// reads the resident state and sums in FP64: total momentum sum m v, kinetic
+// energy sum m v^2 / 2, the conservative DPD potential U = a rc/2 (1 -
+// r/rc)^2 of every non-excluded pair within rc (the potential of Eq.
+// conservative), and the FENE potential -H R0^2/2 ln(1 - r^2/R0^2) of every
+// bond (Eq. fene_force).  Pairs are found by brute force over the box in a
+// balanced half ring (bead i meets i+1 .. i+N/2 mod N), displacements are
+// formed from the cell-relative positions with the minimum image (Lees-
+// Edwards shifted across y), so the result does not depend on the cell list.
+constexpr int kDiagThreads = 256;
+
+__device__ __forceinline__ void diag_disp(const BoxInfo& B, float le_off, bool le, float4 a,
+                                          float4 b, float& rx, float& ry, float& rz) {
+  const int ca = __float_as_int(a.w), cb = __float_as_int(b.w);
+  const int nx = B.nc[0], nxy = B.nc[0] * B.nc[1];
+  const int az = ca / nxy, ay = (ca - az * nxy) / nx, ax = ca - az * nxy - ay * nx;
+  const int bz = cb / nxy, by = (cb - bz * nxy) / nx, bx = cb - bz * nxy - by * nx;
+  rx = static_cast<float>(ax - bx) * B.w[0] + (a.x - b.x);
+  ry = static_cast<float>(ay - by) * B.w[1] + (a.y - b.y);
+  rz = static_cast<float>(az - bz) * B.w[2] + (a.z - b.z);
+  if (ry > 0.5f * B.len[1]) {
+    ry -= B.len[1];
+    if (le) rx -= le_off;
+  } else if (ry < -0.5f * B.len[1]) {
+    ry += B.len[1];
+    if (le) rx += le_off;
+  }
+  rx -= B.len[0] * rintf(rx / B.len[0]);
+  rz -= B.len[2] * rintf(rz / B.len[2]);
+}
+
+__global__ void __launch_bounds__(kDiagThreads) micro_diagnostics_kernel(const MicroArgs A,
+                                                                         double* out) {
+  __shared__ double red[kDiagThreads / 32][7];
+  const int bid = blockIdx.x;
+  const BoxInfo B = A.boxes[bid];
+  const bool le = A.flow == LHMM_FLOW_LEES_EDWARDS;
+  const float le_off = A.state[bid].le_offset;
+  const float4* pos = A.pos + B.off;
+  const float4* vel = A.vel + B.off;
+  const int N = B.n;
+  double s[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  bool over = false;
+  const float rc2 = A.rc * A.rc;
+  for (int i = threadIdx.x; i < N; i += kDiagThreads) {
+    const float4 v = vel[i];
+    const double m = static_cast<double>(A.mass);
+    s[0] += m * v.x;
+    s[1] += m * v.y;
+    s[2] += m * v.z;
+    s[3] += 0.5 * m * (static_cast<double>(v.x) * v.x + static_cast<double>(v.y) * v.y +
+                       static_cast<double>(v.z) * v.z);
+    const float4 pi = pos[i];
+    // half ring: i meets i+1 .. i+N/2 (mod N); with N even, the partner at
+    // distance N/2 is taken by the lower bead only
+    const int half = N / 2;
+    const int last = (N % 2 == 0 && i >= half) ? half - 1 : half;
+    for (int k = 1; k <= last; ++k) {
+      int j = i + k;
+      j -= (j >= N) ? N : 0;
+      float rx, ry, rz;
+      diag_disp(B, le_off, le, pi, __ldg(&pos[j]), rx, ry, rz);
+      const float r2 = rx * rx + ry * ry + rz * rz;
+      if (r2 < rc2) {
+        const int lo = min(i, j), d = max(i, j) - lo;
+        const bool excl = A.excl > 0 && d <= A.excl && lo + d < B.n_poly &&
+                          (lo % A.chain_len) + d < A.chain_len;
+        if (!excl) {
+          const double w = 1.0 - sqrt(static_cast<double>(r2)) / static_cast<double>(A.rc);
+          s[4] += 0.5 * static_cast<double>(A.a) * static_cast<double>(A.rc) * w * w;
+        }
+      }
+    }
+    if (i + 1 < B.n_poly && (i + 1) % A.chain_len != 0) {  // bond (i, i+1)
+      float rx, ry, rz;
+      diag_disp(B, le_off, le, pi, pos[i + 1], rx, ry, rz);
+      double x = (static_cast<double>(rx) * rx + static_cast<double>(ry) * ry +
+                  static_cast<double>(rz) * rz) / (static_cast<double>(A.R0) * A.R0);
+      if (!(x < 1.0)) {
+        x = 0.99;
+        over = true;
+      }
+      s[5] += -0.5 * static_cast<double>(A.H) * static_cast<double>(A.R0) * A.R0 * log(1.0 - x);
+    }
+  }
+  s[6] = over ? 1.0 : 0.0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    double v = s[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 7) {
+    double v = 0.0;
+    for (int w = 0; w < kDiagThreads / 32; ++w) v += red[w][threadIdx.x];
+    red[0][threadIdx.x] = v;  // each thread rewrites only its own column
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double* o = out + 8 * bid;
+    o[0] = red[0][0];
+    o[1] = red[0][1];
+    o[2] = red[0][2];
+    o[3] = red[0][3];
+    o[4] = red[0][4];
+    o[5] = red[0][5];
+    o[6] = red[0][3] + red[0][4] + red[0][5];
+    o[7] = red[0][6] > 0.0 ? 1.0 : 0.0;
+  }
+}
+
 // Launch variants: threads per block and the resident blocks per SM that
 // the register allocation must allow (64 registers/thread for 2048/SM).
 struct Variant {
@@ -1368,6 +1484,16 @@ extern "C" lhmm_status lhmm_micro_advance_dev_count(lhmm_micro_t h, const float*
   const int grid = std::min(max_active, 2 * n_sm);
   LHMM_CK(cudaMemsetAsync(h->work_counter, 0, sizeof(int), s));
   LHMM_CK(launch_subset(h, a, box_idx_dev, grid, s));
+  return LHMM_OK;
+}
+
+extern "C" lhmm_status lhmm_micro_diagnostics(lhmm_micro_t h, double* diag_dev, void* stream) {
+  if (!h || !diag_dev) return LHMM_ERR_ARG;
+  if (h->n_boxes == 0) return LHMM_OK;
+  MicroArgs a = make_args(h);
+  micro_diagnostics_kernel<<<h->n_boxes, kDiagThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+      a, diag_dev);
+  LHMM_CK(cudaGetLastError());
   return LHMM_OK;
 }
 

@@ -85,6 +85,7 @@ def lib():
         L.lhmm_micro_set_state.argtypes = [vp, C.c_int, _D, _F, _F, C.c_uint64, C.c_float]
         L.lhmm_micro_info.argtypes = [vp, _I, C.POINTER(C.c_int64), _I]
         L.lhmm_micro_autotune.argtypes = [vp, vp, C.c_int, vp]
+        L.lhmm_micro_diagnostics.argtypes = [vp, vp, vp]
         L.lhmm_micro_plan.argtypes = [vp, _I, C.c_int, _I, _I, _I, _I]
         L.lhmm_micro_set_variant.argtypes = [vp, C.c_int, C.c_int]
         L.lhmm_sph_create.argtypes = [C.POINTER(SphParams), _F, _F, vp, C.POINTER(vp)]
@@ -227,6 +228,12 @@ class Micro:
         check(lib().lhmm_micro_advance_host(self.h, pL, int(n_steps), ps, pq,
                                             _stream_ptr(stream)), "lhmm_micro_advance_host")
         return stress_host
+
+    def diagnostics(self, diag_dev, stream=None):
+        """FP64 [P_x, P_y, P_z, kinetic, DPD potential, FENE potential, total
+        energy, over-stretch flag] per box into diag_dev (n_boxes x 8)."""
+        check(lib().lhmm_micro_diagnostics(self.h, _ptr(diag_dev), _stream_ptr(stream)),
+              "lhmm_micro_diagnostics")
 
     def sync(self, raise_on_error=True):
         st = np.zeros(max(self.n_boxes, 1), np.uint32)

@@ -51,4 +51,5 @@ def pytest_sessionfinish(session, exitstatus):
         fh.write("| test | result | measured FP32-vs-FP64 error | tolerance | unit |\n")
         fh.write("|---|---|---|---|---|\n")
         for test, result, err, tol, unit in _PARITY_ROWS:
-            fh.write("| %s | %s | %.3g | %.3g | %s |\n" % (test, result, err, tol, unit))
+            fh.write("| %s | %s | %.3g | %.3g | %s |\n"
+                     % (test, result, err, tol, unit.replace("|", "\\|")))
