@@ -382,6 +382,17 @@ lhmm_status lhmm_closure_get_params(lhmm_closure_t c, int member, float* host);
 lhmm_status lhmm_closure_set_params(lhmm_closure_t c, int member, const float* host);
 lhmm_status lhmm_closure_get_grad(lhmm_closure_t c, int member, float* host);
 lhmm_status lhmm_closure_info(lhmm_closure_t c, int64_t* n_params_per_member, int64_t* steps);
+/* Tensor-core path of the closure's products: 1 (the default) runs them on
+ * the fifth-generation tensor cores (tcgen05.mma with the accumulator in
+ * tensor memory, operands staged by TMA); 0 on the warp-level mma.sync path
+ * kept for comparison.  Both take BF16 operands and accumulate in FP32, so
+ * they differ only by the order of the FP32 sums.  Other values return
+ * LHMM_ERR_ARG. */
+lhmm_status lhmm_closure_set_gemm(lhmm_closure_t c, int path);
+/* Wait for the device; returns LHMM_ERR_TIMEOUT (and clears it) if a
+ * tensor-core product gave up a bounded wait since the last call, which
+ * leaves its outputs undefined.  Synchronous. */
+lhmm_status lhmm_closure_sync(lhmm_closure_t c);
 
 /* ------------------------------------------------------------------------
  * Surrogate-gated macro step (not in the paper).  With a closure attached,

@@ -16,6 +16,7 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda.h>  // CUtensorMap and its enums (the encoder comes from the driver at run time)
 #include <cuda_bf16.h>
 
 #include "lhmm_common.cuh"
@@ -54,6 +55,33 @@ struct GemmArgs {
 __device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float x) {
   return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
+}
+
+// The fused epilogue of one element (m, n) of member `member` (the same for
+// both GEMM kernels below).
+template <int EPI>
+__device__ __forceinline__ void store_epi(const GemmArgs& g, int member, int m, int n, float v) {
+  if (EPI == EPI_DW) {
+    float* c = g.Cf + g.sC * member + static_cast<long long>(m) * g.ldc + n;
+    if (g.k_split > 1) atomicAdd(c, v);
+    else *c = v;
+  } else if (EPI == EPI_FWD_OUT) {
+    v += g.bias[g.sBias * member + n];
+    g.Cf[g.sC * member + static_cast<long long>(m) * g.ldc + n] = v;
+  } else if (EPI == EPI_FWD_HIDDEN || EPI == EPI_FWD_INFER) {
+    const float z = v + g.bias[g.sBias * member + n];
+    const bf16 h = __float2bfloat16(gelu(z));
+    g.Hb[g.sH * member + static_cast<long long>(m) * g.ldh + n] = h;
+    if (EPI == EPI_FWD_HIDDEN) {
+      g.Cf[g.sC * member + static_cast<long long>(m) * g.ldc + n] = z;
+      g.HTb[g.sHT * member + static_cast<long long>(n) * g.ldht + m] = h;
+    }
+  } else {  // EPI_BWD_DH: dZ_{l-1} = dH_{l-1} * GELU'(Z_{l-1})
+    const float z = g.Zprev[g.sZ * member + static_cast<long long>(m) * g.ldz + n];
+    const bf16 dz = __float2bfloat16(v * gelu_grad(z));
+    g.Hb[g.sH * member + static_cast<long long>(m) * g.ldh + n] = dz;
+    g.HTb[g.sHT * member + static_cast<long long>(n) * g.ldht + m] = dz;
+  }
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
@@ -163,28 +191,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_nt(const GemmArgs g) {
         const int m = m0 + wm * 32 + i * 16 + (lane >> 2) + ((q >> 1) << 3);
         const int n = n0 + wn * 64 + j * 8 + ((lane & 3) << 1) + (q & 1);
         if (m >= g.M || n >= g.N) continue;
-        float v = acc[i][j][q];
-        if (EPI == EPI_DW) {
-          float* c = g.Cf + g.sC * member + static_cast<long long>(m) * g.ldc + n;
-          if (g.k_split > 1) atomicAdd(c, v);
-          else *c = v;
-        } else if (EPI == EPI_FWD_OUT) {
-          v += g.bias[g.sBias * member + n];
-          g.Cf[g.sC * member + static_cast<long long>(m) * g.ldc + n] = v;
-        } else if (EPI == EPI_FWD_HIDDEN || EPI == EPI_FWD_INFER) {
-          const float z = v + g.bias[g.sBias * member + n];
-          const bf16 h = __float2bfloat16(gelu(z));
-          g.Hb[g.sH * member + static_cast<long long>(m) * g.ldh + n] = h;
-          if (EPI == EPI_FWD_HIDDEN) {
-            g.Cf[g.sC * member + static_cast<long long>(m) * g.ldc + n] = z;
-            g.HTb[g.sHT * member + static_cast<long long>(n) * g.ldht + m] = h;
-          }
-        } else {  // EPI_BWD_DH: dZ_{l-1} = dH_{l-1} * GELU'(Z_{l-1})
-          const float z = g.Zprev[g.sZ * member + static_cast<long long>(m) * g.ldz + n];
-          const bf16 dz = __float2bfloat16(v * gelu_grad(z));
-          g.Hb[g.sH * member + static_cast<long long>(m) * g.ldh + n] = dz;
-          g.HTb[g.sHT * member + static_cast<long long>(n) * g.ldht + m] = dz;
-        }
+        store_epi<EPI>(g, member, m, n, acc[i][j][q]);
       }
     }
   }
@@ -194,6 +201,335 @@ template <int EPI>
 cudaError_t run_gemm(const GemmArgs& g, int members, cudaStream_t s) {
   dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, members * g.k_split);
   gemm_nt<EPI><<<grid, GEMM_THREADS, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- tcgen05 path
+// The same NT products on the fifth-generation tensor cores: per block a
+// 128 x 128 tile of C, its FP32 accumulator in tensor memory (128 lanes x 128
+// columns).  One thread issues everything asynchronous: TMA loads of 128-row
+// x 64-column BF16 boxes of A and B (128-byte swizzle, zero fill past the
+// matrix edges, one 3D tensor map per operand whose third axis is the
+// ensemble member) into a ring of four stages, and per stage four
+// tcgen05.mma (M = 128, N = 128, K = 16) whose completion frees the stage
+// through tcgen05.commit.  Then the four warps copy their 32 accumulator
+// rows (tcgen05.ld) into the stage memory, now idle, and the block runs the
+// fused epilogue of gemm_nt from there: row-major outputs with the lanes of
+// a warp along a row, transposed outputs (H^T, dZ^T) with the lanes along a
+// column, so every store of a warp is contiguous.  Every wait on an mbarrier
+// gives up after a bounded number of polls and raises a flag.
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 3, TC_THREADS = 128;
+constexpr int TC_LDT = TC_BN + 1;  // staged tile row stride (floats): conflict-free both ways
+constexpr uint32_t TC_TILE_BYTES = TC_BM * TC_BK * 2;          // 16 KB per operand and stage
+constexpr uint32_t TC_STAGE_BYTES = 2 * TC_TILE_BYTES;
+constexpr size_t TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024;   // + room to align to 1024 B
+constexpr uint32_t TC_WAIT_POLLS = 1u << 22;                    // try_wait polls before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+// wait for the phase of the given parity to complete; false after the poll limit
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (uint32_t it = 0; it < TC_WAIT_POLLS; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+// shared-memory matrix descriptor of a K-major operand tile stored as the
+// TMA's 128-byte swizzle writes it: rows of 128 bytes (64 BF16 along K),
+// groups of 8 rows 1024 bytes apart; the start address steps 32 bytes per
+// K = 16 inside a row
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+  uint64_t d = static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= static_cast<uint64_t>(1) << 16;                            // leading byte offset (16 B)
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;                    // stride byte offset
+  d |= static_cast<uint64_t>(1) << 46;                            // descriptor version
+  d |= static_cast<uint64_t>(2) << 61;                            // 128-byte swizzle
+  return d;
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N = 128, M = 128
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                              (static_cast<uint32_t>(TC_BN >> 3) << 17) |
+                              (static_cast<uint32_t>(TC_BM >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kTcIdesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+      " [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+static_assert(TC_BM * TC_LDT * 4 <= TC_STAGES * TC_STAGE_BYTES, "staged tile fits the stages");
+
+// row pass of the fused epilogue for element (m, n): writes the row-major
+// outputs and returns the value a transposed output takes (H or dZ, rounded
+// to BF16) for the column pass
+template <int EPI>
+__device__ __forceinline__ float epi_row(const GemmArgs& g, int member, int m, int n, float v) {
+  if (EPI == EPI_DW) {
+    float* c = g.Cf + g.sC * member + static_cast<long long>(m) * g.ldc + n;
+    if (g.k_split > 1) atomicAdd(c, v);
+    else *c = v;
+    return 0.f;
+  } else if (EPI == EPI_FWD_OUT) {
+    g.Cf[g.sC * member + static_cast<long long>(m) * g.ldc + n] = v + g.bias[g.sBias * member + n];
+    return 0.f;
+  } else if (EPI == EPI_FWD_HIDDEN || EPI == EPI_FWD_INFER) {
+    const float z = v + g.bias[g.sBias * member + n];
+    const bf16 h = __float2bfloat16(gelu(z));
+    g.Hb[g.sH * member + static_cast<long long>(m) * g.ldh + n] = h;
+    if (EPI == EPI_FWD_HIDDEN) g.Cf[g.sC * member + static_cast<long long>(m) * g.ldc + n] = z;
+    return __bfloat162float(h);
+  } else {  // EPI_BWD_DH
+    const float z = g.Zprev[g.sZ * member + static_cast<long long>(m) * g.ldz + n];
+    const bf16 dz = __float2bfloat16(v * gelu_grad(z));
+    g.Hb[g.sH * member + static_cast<long long>(m) * g.ldh + n] = dz;
+    return __bfloat162float(dz);
+  }
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(TC_THREADS, 2)
+    gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+            const GemmArgs g, int* err) {
+  extern __shared__ unsigned char tc_smem_raw[];
+  __shared__ __align__(8) uint64_t bars[2 * TC_STAGES + 1];
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int member = blockIdx.z / g.k_split, split = blockIdx.z % g.k_split;
+  const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TC_BN;
+  const int kt_all = (g.K + TC_BK - 1) / TC_BK;
+  const int kt_per = (kt_all + g.k_split - 1) / g.k_split;
+  const int kt0 = split * kt_per, nk = max(0, min(kt_all, kt0 + kt_per) - kt0);
+  const uint32_t base = (smem_u32(tc_smem_raw) + 1023u) & ~1023u;  // swizzle atoms are 1024 B
+  const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[TC_STAGES]);
+  const uint32_t done = smem_u32(&bars[2 * TC_STAGES]);
+  if (tid == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {  // 128 TMEM columns: the 128 x 128 FP32 accumulator
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(TC_BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  __shared__ int ok_s;
+  if (tid == 0) {
+    bool ok = true;
+    int issued = 0;     // k-tiles whose loads were issued
+    bool mma = false;   // whether any MMA was issued
+    for (int it = 0; it < nk + TC_STAGES - 1 && ok; ++it) {
+      if (it < nk) {  // produce k-tile `it`
+        const int s = it % TC_STAGES;
+        if (it >= TC_STAGES) ok = mbar_wait(empty0 + 8 * s, ((it / TC_STAGES) - 1) & 1);
+        if (!ok) break;
+        mbar_expect_tx(full0 + 8 * s, TC_STAGE_BYTES);
+        const uint32_t sa = base + s * TC_STAGE_BYTES, sb = sa + TC_TILE_BYTES;
+        const int kx = (kt0 + it) * TC_BK;
+        tma_load_3d(sa, &mapA, full0 + 8 * s, kx, m0, member);
+        tma_load_3d(sb, &mapB, full0 + 8 * s, kx, n0, member);
+        issued = it + 1;
+      }
+      const int kc = it - (TC_STAGES - 1);
+      if (kc >= 0) {  // consume k-tile kc
+        const int s = kc % TC_STAGES;
+        ok = mbar_wait(full0 + 8 * s, (kc / TC_STAGES) & 1);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t sa = base + s * TC_STAGE_BYTES, sb = sa + TC_TILE_BYTES;
+        const uint64_t da = umma_desc_sw128(sa), db = umma_desc_sw128(sb);
+#pragma unroll
+        for (int kk = 0; kk < TC_BK / 16; ++kk)  // +32 bytes per K = 16: +2 in the address field
+          umma_bf16(tmem, da + 2 * kk, db + 2 * kk, (kc > 0 || kk > 0) ? 1u : 0u);
+        umma_commit(empty0 + 8 * s);
+        mma = true;
+      }
+    }
+    // `done` completes when every MMA issued so far has (the epilogue waits
+    // for it; on the error path it keeps TMEM alive until they finish)
+    if (mma) umma_commit(done);
+    if (!ok) {
+      atomicExch(err, 1);
+      if (mma) mbar_wait(done, 0);
+      // and the loads already issued land before the block's memory goes away
+      for (int k = 0; k < issued; ++k) mbar_wait(full0 + 8 * (k % TC_STAGES), (k / TC_STAGES) & 1);
+    }
+    ok_s = (ok && mma) ? 1 : 0;
+  }
+  __syncthreads();
+  const bool have = ok_s && mbar_wait(done, 0);
+  if (ok_s && !have) atomicExch(err, 1);
+  // the accumulator tile, staged in the idle stage memory (all loads have
+  // landed and every MMA has read its operands once `done` completed)
+  float* const tile = reinterpret_cast<float*>(tc_smem_raw + (base - smem_u32(tc_smem_raw)));
+  if (have) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // warp w holds accumulator rows 32 w .. 32 w + 31 (TMEM lanes)
+    const int r = 32 * warp + lane;
+    const uint32_t trow = tmem + (static_cast<uint32_t>(32 * warp) << 16);
+#pragma unroll 1
+    for (int c = 0; c < TC_BN; c += 16) {
+      float v[16];
+      tmem_ld16(trow + static_cast<uint32_t>(c), v);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) tile[r * TC_LDT + c + k] = v[k];
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (have) {
+    // row pass: lanes along n
+    for (int r = warp; r < TC_BM; r += TC_THREADS / 32) {
+      const int m = m0 + r;
+      if (m >= g.M) continue;
+#pragma unroll
+      for (int j = 0; j < TC_BN / 32; ++j) {
+        const int nl = 32 * j + lane, n = n0 + nl;
+        if (n < g.N) tile[r * TC_LDT + nl] = epi_row<EPI>(g, member, m, n, tile[r * TC_LDT + nl]);
+      }
+    }
+    if (EPI == EPI_FWD_HIDDEN || EPI == EPI_BWD_DH) {  // column pass: lanes along m
+      __syncthreads();
+      for (int nl = warp; nl < TC_BN; nl += TC_THREADS / 32) {
+        const int n = n0 + nl;
+        if (n >= g.N) continue;
+#pragma unroll
+        for (int j = 0; j < TC_BM / 32; ++j) {
+          const int r = 32 * j + lane, m = m0 + r;
+          if (m < g.M)
+            g.HTb[g.sHT * member + static_cast<long long>(n) * g.ldht + m] =
+                __float2bfloat16(tile[r * TC_LDT + nl]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN)
+                 : "memory");
+  }
+}
+
+// cuTensorMapEncodeTiled from the driver (no link against libcuda)
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 3D map (K, rows, member) of a K-major BF16 operand with leading dimension
+// ld and member stride sm (elements), boxes of 64 x 128 x 1
+bool make_map(CUtensorMap* map, const bf16* ptr, int K, int rows, int ld, long long sm, int members) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  if ((reinterpret_cast<uintptr_t>(ptr) & 15) || (ld * 2) % 16 || (sm * 2) % 16) return false;
+  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(K), static_cast<cuuint64_t>(rows),
+                              static_cast<cuuint64_t>(members)};
+  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(ld) * 2, static_cast<cuuint64_t>(sm) * 2};
+  const cuuint32_t box[3] = {TC_BK, TC_BM, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(ptr), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+cudaError_t tc_attributes() {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(gemm_tc<EPI_FWD_HIDDEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(TC_SMEM))) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(gemm_tc<EPI_FWD_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(TC_SMEM))) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(gemm_tc<EPI_BWD_DH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(TC_SMEM))) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(gemm_tc<EPI_DW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(TC_SMEM))) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(gemm_tc<EPI_FWD_INFER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(TC_SMEM))) != cudaSuccess)
+    return e;
+  return cudaSuccess;
+}
+
+template <int EPI>
+cudaError_t run_gemm_tc(const GemmArgs& g, int members, int* err, cudaStream_t s) {
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, g.A, g.K, g.M, g.lda, g.sA, members) ||
+      !make_map(&mb, g.B, g.K, g.N, g.ldb, g.sB, members))
+    return cudaErrorInvalidValue;
+  dim3 grid((g.N + TC_BN - 1) / TC_BN, (g.M + TC_BM - 1) / TC_BM, members * g.k_split);
+  gemm_tc<EPI><<<grid, TC_THREADS, TC_SMEM, s>>>(ma, mb, g, err);
   return cudaGetLastError();
 }
 
@@ -339,6 +675,8 @@ struct lhmm_closure_s {
   std::vector<float*> Z;
   float* Y = nullptr;
   float* loss = nullptr;
+  int gemm_path = 1;     // 1: tcgen05 + TMA (gemm_tc), 0: mma.sync (gemm_nt)
+  int* tc_err = nullptr; // set by gemm_tc when a bounded wait gives up
 };
 
 namespace {
@@ -379,6 +717,7 @@ void free_closure(lhmm_closure_s* c) {
   cudaFree(c->out_scale);
   cudaFree(c->out_iscale);
   cudaFree(c->loss);
+  cudaFree(c->tc_err);
   delete c;
 }
 
@@ -411,6 +750,12 @@ cudaError_t ensure_ws(lhmm_closure_s* c, int rows) {
   return cudaSuccess;
 }
 
+template <int EPI>
+cudaError_t gemm(const lhmm_closure_s* c, const GemmArgs& g, cudaStream_t s) {
+  return c->gemm_path == 1 ? run_gemm_tc<EPI>(g, c->members, c->tc_err, s)
+                           : run_gemm<EPI>(g, c->members, s);
+}
+
 // forward over `rows` inputs already in Xb/XTb; train=1 keeps Z and H^T
 cudaError_t forward(lhmm_closure_s* c, int rows, bool train, cudaStream_t s) {
   const long long R = rows, Hd = c->hidden;
@@ -434,7 +779,7 @@ cudaError_t forward(lhmm_closure_s* c, int rows, bool train, cudaStream_t s) {
       g.Cf = c->Y;
       g.ldc = c->out_pad;
       g.sC = R * c->out_pad;
-      e = run_gemm<EPI_FWD_OUT>(g, c->members, s);
+      e = gemm<EPI_FWD_OUT>(c, g, s);
     } else {
       g.Hb = c->Hb[l];
       g.ldh = c->hidden;
@@ -445,7 +790,7 @@ cudaError_t forward(lhmm_closure_s* c, int rows, bool train, cudaStream_t s) {
       g.Cf = c->Z[l];
       g.ldc = c->hidden;
       g.sC = R * Hd;
-      e = train ? run_gemm<EPI_FWD_HIDDEN>(g, c->members, s) : run_gemm<EPI_FWD_INFER>(g, c->members, s);
+      e = train ? gemm<EPI_FWD_HIDDEN>(c, g, s) : gemm<EPI_FWD_INFER>(c, g, s);
     }
     if (e != cudaSuccess) return e;
   }
@@ -477,7 +822,7 @@ cudaError_t backward(lhmm_closure_s* c, int rows, cudaStream_t s) {
     g.ldc = c->L.in_pad[l];
     g.sC = c->n_per;
     g.k_split = std::max(1, std::min(16, rows / 512));
-    if ((e = run_gemm<EPI_DW>(g, c->members, s)) != cudaSuccess) return e;
+    if ((e = gemm<EPI_DW>(c, g, s)) != cudaSuccess) return e;
     // db_l = column sums of dZ_l
     {
       dim3 grid((Np + 7) / 8, c->members);
@@ -506,7 +851,7 @@ cudaError_t backward(lhmm_closure_s* c, int rows, cudaStream_t s) {
     h.ldht = rows;
     h.sHT = R * Hd;
     h.k_split = 1;
-    if ((e = run_gemm<EPI_BWD_DH>(h, c->members, s)) != cudaSuccess) return e;
+    if ((e = gemm<EPI_BWD_DH>(c, h, s)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -562,7 +907,10 @@ extern "C" lhmm_status lhmm_closure_create(int members, int in_dim, int hidden, 
       (e = cudaMalloc(&c->in_istd, sizeof(float) * in_dim)) != cudaSuccess ||
       (e = cudaMalloc(&c->out_scale, sizeof(float) * 8)) != cudaSuccess ||
       (e = cudaMalloc(&c->out_iscale, sizeof(float) * 8)) != cudaSuccess ||
-      (e = cudaMalloc(&c->loss, sizeof(float) * 16)) != cudaSuccess) {
+      (e = cudaMalloc(&c->loss, sizeof(float) * 16)) != cudaSuccess ||
+      (e = cudaMalloc(&c->tc_err, sizeof(int))) != cudaSuccess ||
+      (e = cudaMemset(c->tc_err, 0, sizeof(int))) != cudaSuccess ||
+      (e = tc_attributes()) != cudaSuccess) {
     free_closure(c);
     return lhmm_cuda_error(e);
   }
@@ -764,6 +1112,24 @@ extern "C" lhmm_status lhmm_closure_get_grad(lhmm_closure_t c, int member, float
   if (!c) return LHMM_ERR_ARG;
   return copy_member(c, member, host, false, c->G);
 }
+extern "C" lhmm_status lhmm_closure_set_gemm(lhmm_closure_t c, int path) {
+  if (!c || (path != 0 && path != 1)) return LHMM_ERR_ARG;
+  c->gemm_path = path;
+  return LHMM_OK;
+}
+
+extern "C" lhmm_status lhmm_closure_sync(lhmm_closure_t c) {
+  if (!c) return LHMM_ERR_ARG;
+  LHMM_CK(cudaDeviceSynchronize());
+  int flag = 0;
+  LHMM_CK(cudaMemcpy(&flag, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    LHMM_CK(cudaMemset(c->tc_err, 0, sizeof(int)));
+    return LHMM_ERR_TIMEOUT;
+  }
+  return LHMM_OK;
+}
+
 extern "C" lhmm_status lhmm_closure_info(lhmm_closure_t c, int64_t* n_params_per_member,
                                          int64_t* steps) {
   if (!c) return LHMM_ERR_ARG;

@@ -118,6 +118,8 @@ def lib():
         L.lhmm_closure_set_params.argtypes = [vp, C.c_int, _F]
         L.lhmm_closure_get_grad.argtypes = [vp, C.c_int, _F]
         L.lhmm_closure_info.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        L.lhmm_closure_set_gemm.argtypes = [vp, C.c_int]
+        L.lhmm_closure_sync.argtypes = [vp]
         _lib = L
     return _lib
 
@@ -458,6 +460,13 @@ class Closure:
             self.close()
         except Exception:
             pass
+
+    def set_gemm(self, path):
+        """1: tcgen05 tensor-core products (default); 0: mma.sync products."""
+        check(lib().lhmm_closure_set_gemm(self.h, int(path)), "lhmm_closure_set_gemm")
+
+    def sync(self):
+        check(lib().lhmm_closure_sync(self.h), "lhmm_closure_sync")
 
     def set_normalization(self, in_mean, in_std, out_scale):
         a, pa = _np(in_mean, np.float32)

@@ -143,3 +143,33 @@ def test_calibration_folds_linear_map_into_output_layer():
     c.infer(Xd, mean, spread)
     assert np.allclose(mean.cpu().numpy(), T, rtol=2e-3, atol=2e-3 * np.abs(T).max())
     c.close()
+
+
+@pytest.mark.parametrize("rows", [96, 160, 4096])
+def test_tensor_core_path_matches_mma_sync_path(rows, parity_report):
+    # the tcgen05 products (accumulator in tensor memory, TMA-staged operands)
+    # against the mma.sync products on the same BF16 operands: both accumulate
+    # in FP32, so outputs differ only by the order of the sums (and the BF16
+    # rounding of hidden activations that this can flip); gradients likewise.
+    # rows = 96 and 160 leave a partial 128-row tile.
+    c = _closure(members=3, seed=7)
+    rng = np.random.default_rng(rows)
+    X = torch.from_numpy(rng.normal(size=(rows, 67)).astype(np.float32)).cuda()
+    T = torch.from_numpy(rng.normal(size=(rows, 3)).astype(np.float32)).cuda()
+    out, grads = {}, {}
+    for path in (0, 1):
+        c.set_gemm(path)
+        out[path] = c.forward_members(X)
+        c.train_step(X, T, rows, lr=0.0)
+        c.sync()
+        grads[path] = [c.get_grad(m).astype(np.float64) for m in range(3)]
+    y0, y1 = out[0], out[1]
+    err = np.abs(y1 - y0).max() / np.abs(y0).max()
+    assert err <= 2e-3, err
+    parity_report("tcgen05 vs mma.sync forward, %d rows" % rows, err, 2e-3, "max |dy| / max |y|")
+    for m in range(3):
+        g0, g1 = grads[0][m], grads[1][m]
+        rel = np.linalg.norm(g1 - g0) / np.linalg.norm(g0)
+        assert rel <= 1e-2, (m, rel)
+    parity_report("tcgen05 vs mma.sync gradient, %d rows" % rows, rel, 1e-2, "|dg| / |g| (L2)")
+    c.close()
