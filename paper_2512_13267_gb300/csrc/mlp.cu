@@ -218,7 +218,7 @@ cudaError_t run_gemm(const GemmArgs& g, int members, cudaStream_t s) {
 // a warp along a row, transposed outputs (H^T, dZ^T) with the lanes along a
 // column, so every store of a warp is contiguous.  Every wait on an mbarrier
 // gives up after a bounded number of polls and raises a flag.
-constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 3, TC_THREADS = 128;
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 3, TC_THREADS = 256;
 constexpr int TC_LDT = TC_BN + 1;  // staged tile row stride (floats): conflict-free both ways
 constexpr uint32_t TC_TILE_BYTES = TC_BM * TC_BK * 2;          // 16 KB per operand and stage
 constexpr uint32_t TC_STAGE_BYTES = 2 * TC_TILE_BYTES;
@@ -310,28 +310,29 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 
 static_assert(TC_BM * TC_LDT * 4 <= TC_STAGES * TC_STAGE_BYTES, "staged tile fits the stages");
 
-// row pass of the fused epilogue for element (m, n): writes the row-major
-// outputs and returns the value a transposed output takes (H or dZ, rounded
-// to BF16) for the column pass
+// row pass of the fused epilogue for element (m, n), given its input `in`
+// (the bias of column n, or Z_{l-1}(m, n) for the backward product): writes
+// the row-major outputs and returns the value a transposed output takes (H
+// or dZ, rounded to BF16) for the column pass
 template <int EPI>
-__device__ __forceinline__ float epi_row(const GemmArgs& g, int member, int m, int n, float v) {
+__device__ __forceinline__ float epi_row(const GemmArgs& g, int member, int m, int n, float v,
+                                         float in) {
   if (EPI == EPI_DW) {
     float* c = g.Cf + g.sC * member + static_cast<long long>(m) * g.ldc + n;
     if (g.k_split > 1) atomicAdd(c, v);
     else *c = v;
     return 0.f;
   } else if (EPI == EPI_FWD_OUT) {
-    g.Cf[g.sC * member + static_cast<long long>(m) * g.ldc + n] = v + g.bias[g.sBias * member + n];
+    g.Cf[g.sC * member + static_cast<long long>(m) * g.ldc + n] = v + in;
     return 0.f;
   } else if (EPI == EPI_FWD_HIDDEN || EPI == EPI_FWD_INFER) {
-    const float z = v + g.bias[g.sBias * member + n];
+    const float z = v + in;
     const bf16 h = __float2bfloat16(gelu(z));
     g.Hb[g.sH * member + static_cast<long long>(m) * g.ldh + n] = h;
     if (EPI == EPI_FWD_HIDDEN) g.Cf[g.sC * member + static_cast<long long>(m) * g.ldc + n] = z;
     return __bfloat162float(h);
   } else {  // EPI_BWD_DH
-    const float z = g.Zprev[g.sZ * member + static_cast<long long>(m) * g.ldz + n];
-    const bf16 dz = __float2bfloat16(v * gelu_grad(z));
+    const bf16 dz = __float2bfloat16(v * gelu_grad(in));
     g.Hb[g.sH * member + static_cast<long long>(m) * g.ldh + n] = dz;
     return __bfloat162float(dz);
   }
@@ -422,11 +423,13 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   float* const tile = reinterpret_cast<float*>(tc_smem_raw + (base - smem_u32(tc_smem_raw)));
   if (have) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // warp w holds accumulator rows 32 w .. 32 w + 31 (TMEM lanes)
-    const int r = 32 * warp + lane;
-    const uint32_t trow = tmem + (static_cast<uint32_t>(32 * warp) << 16);
+    // warp w may read TMEM lanes 32 (w % 4) .. + 31 (accumulator rows); the
+    // two warps of a lane quarter split the columns
+    const int r = 32 * (warp & 3) + lane;
+    const int cbeg = (warp >> 2) * (TC_BN / 2);
+    const uint32_t trow = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
 #pragma unroll 1
-    for (int c = 0; c < TC_BN; c += 16) {
+    for (int c = cbeg; c < cbeg + TC_BN / 2; c += 16) {
       float v[16];
       tmem_ld16(trow + static_cast<uint32_t>(c), v);
 #pragma unroll
@@ -436,14 +439,37 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (have) {
-    // row pass: lanes along n
-    for (int r = warp; r < TC_BM; r += TC_THREADS / 32) {
-      const int m = m0 + r;
-      if (m >= g.M) continue;
+    // row pass: lanes along n, four rows at a time with their inputs loaded
+    // ahead of the arithmetic (the bias once per column)
+    constexpr int NJ = TC_BN / 32, RB = 4;
+    float bias[NJ];
 #pragma unroll
-      for (int j = 0; j < TC_BN / 32; ++j) {
-        const int nl = 32 * j + lane, n = n0 + nl;
-        if (n < g.N) tile[r * TC_LDT + nl] = epi_row<EPI>(g, member, m, n, tile[r * TC_LDT + nl]);
+    for (int j = 0; j < NJ; ++j) {
+      const int n = n0 + 32 * j + lane;
+      bias[j] = (EPI != EPI_DW && EPI != EPI_BWD_DH && n < g.N) ? g.bias[g.sBias * member + n] : 0.f;
+    }
+    const float* __restrict__ zp = g.Zprev + (EPI == EPI_BWD_DH ? g.sZ * member : 0);
+    for (int r0 = warp * RB; r0 < TC_BM; r0 += RB * (TC_THREADS / 32)) {
+      float in[RB][NJ];
+#pragma unroll
+      for (int rr = 0; rr < RB; ++rr)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          const int m = m0 + r0 + rr, n = n0 + 32 * j + lane;
+          in[rr][j] = bias[j];
+          if (EPI == EPI_BWD_DH)
+            in[rr][j] = (m < g.M && n < g.N) ? zp[static_cast<long long>(m) * g.ldz + n] : 0.f;
+        }
+#pragma unroll
+      for (int rr = 0; rr < RB; ++rr) {
+        const int r = r0 + rr, m = m0 + r;
+        if (m >= g.M) continue;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          const int nl = 32 * j + lane, n = n0 + nl;
+          if (n < g.N)
+            tile[r * TC_LDT + nl] = epi_row<EPI>(g, member, m, n, tile[r * TC_LDT + nl], in[rr][j]);
+        }
       }
     }
     if (EPI == EPI_FWD_HIDDEN || EPI == EPI_BWD_DH) {  // column pass: lanes along m
