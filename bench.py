@@ -292,6 +292,47 @@ def macro_step_rate(steps=10, warmup=2):
     return out
 
 
+def sharded_macro_rate(world, rank, steps=10, warmup=2):
+    """LHMM macro-steps/s of one coupled reverse-Poiseuille channel (the
+    `secondary` workload) spread over the ranks: SPH replicated, the 2048
+    boxes in bead-balanced ranges, one NCCL all-gather of the n x 6 stresses
+    per macro step (strong scaling of one system)."""
+    import torch
+    import torch.distributed as dist
+    from paper_2512_13267_gb300 import lhmm, sharding, synth
+    U_o, c_fac, eta_s, alpha, k_micro, dt_dpd = 0.25, 10.0, 0.1, 0.01, 50, 0.01
+    cfg, batch = synth.coupled_channel(U_o=U_o, c_factor=c_fac, eta_s=eta_s,
+                                       delta_t=k_micro * dt_dpd)
+    n, M = cfg["pos"].shape[0], cfg["substeps"]
+    sp = lhmm.sph_params(n, 0, Lx=cfg["Lx"], Ly=cfg["Ly"], h=cfg["h"], mass=cfg["mass"],
+                         rho0=1.0, c=cfg["c"], theta_pb=0.1, eta_s=eta_s, dt=cfg["dt"],
+                         body_force=(cfg["body_force"], 0.0),
+                         body_mode=lhmm.SPH_BODY_REVERSE_POISEUILLE)
+    sph = lhmm.Sph(sp, cfg["pos"], cfg["vel"])
+    ranges = sharding.partition_boxes(batch.n_beads, world)
+    lo, hi = ranges[rank]
+    micro = lhmm.Micro.from_batch(lhmm.dpd_params(flow="afbc", seed=3, alpha=alpha),
+                                  batch.boxes(lo, hi), box_id_offset=lo)
+    drv = sharding.ShardedCoupled(sharding.GpuSph(sph, n, M), sharding.GpuMicro(micro, k_micro),
+                                  ranges, torch.zeros((n, 6), dtype=torch.float64, device="cuda"))
+    drv.step(warmup)
+    torch.cuda.synchronize()
+    dist.barrier()
+    t0 = time.perf_counter()
+    drv.step(steps)
+    torch.cuda.synchronize()
+    dist.barrier()
+    t = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    micro.close()
+    sph.close()
+    return {"metric": "LHMM macro-steps/s, one coupled channel sharded over the ranks",
+            "value": steps / float(t.item()), "unit": "macro-steps/s", "ranks": world,
+            "boxes_per_rank": [b - a for a, b in ranges], "scaling": "strong",
+            "workload": "coupled reverse-Poiseuille channel 64x32 SPH x 1500-bead AFBC boxes, "
+                        "k'=50, M=%d; SPH replicated, boxes sharded, stress all-gather" % M}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -498,6 +539,8 @@ def main():
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": desc}
     micro.close()
+    if world > 1 and not args.no_macro and args.uniform_edge <= 0:
+        line["coupled_sharded"] = sharded_macro_rate(world, rank)
     if rank == 0 and not args.no_macro and args.uniform_edge <= 0:
         line["secondary"] = macro_step_rate()
         from paper_2512_13267_gb300 import flows

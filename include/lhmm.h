@@ -105,6 +105,10 @@ typedef struct {
   const int* n_beads;    /* host, n_boxes; 0 <= n < 65536 */
   const int* n_chains;   /* host, n_boxes; n_chains * chain_len <= n_beads */
   int chain_len;         /* N_d >= 2 (ignored when every n_chains is 0) */
+  int box_id_offset;     /* >= 0: box b of this batch keys its random stream as box
+                            box_id_offset + b, so a batch that holds boxes lo..hi-1 of a
+                            larger system (one rank's share) draws the same noise as
+                            those boxes do in one batch of the whole system; 0 otherwise */
 } lhmm_batch_desc;
 
 typedef struct lhmm_micro_s* lhmm_micro_t;

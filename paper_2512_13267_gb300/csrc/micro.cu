@@ -83,6 +83,7 @@ struct MicroArgs {
   int afbc_peculiar;         // BC beads keep their velocity about their cell's BC mean
   int max_beads, max_cells;
   int n_boxes;
+  int id_base;               // random-stream id of box 0 (lhmm_batch_desc.box_id_offset)
   int* work_counter;         // persistent mode: next work item (NULL: one block per item)
   const int* n_items_dev;    // persistent mode: device-side item count
   int max_items;             // persistent mode: capacity of the item list
@@ -288,7 +289,7 @@ __device__ __forceinline__ void micro_box(const MicroArgs& A, const int bid) {
   const float le0 = A.state[bid].le_offset;
   // key (seed_lo, seed_hi ^ box): distinct (seed, box) pairs with seeds below
   // 2^32 get distinct keys, so consecutive seeds never share a box's noise
-  const uint32_t k0 = A.seed_lo, k1 = A.seed_hi ^ static_cast<uint32_t>(bid);
+  const uint32_t k0 = A.seed_lo, k1 = A.seed_hi ^ static_cast<uint32_t>(A.id_base + bid);
   const float hx = 0.5f * sB.len[0], hy = 0.5f * sB.len[1], hz = 0.5f * sB.len[2];
   const unsigned lt_mask = (1u << lane) - 1u;
   unsigned status = 0;
@@ -1074,6 +1075,7 @@ struct SizeClass {
 struct lhmm_micro_s {
   lhmm_dpd_params p;
   int n_boxes = 0, chain_len = 0, max_beads = 0, max_cells = 0;
+  int id_base = 0;  // random-stream id of box 0
   long long total = 0;
   std::vector<BoxInfo> info;
   BoxInfo* info_d = nullptr;
@@ -1219,6 +1221,7 @@ MicroArgs make_args(const lhmm_micro_s* h) {
   a.max_beads = h->max_beads;
   a.max_cells = h->max_cells;
   a.n_boxes = h->n_boxes;
+  a.id_base = h->id_base;
   a.gm = h->gm;
   a.gm_stride = h->gm_stride;
   return a;
@@ -1267,6 +1270,7 @@ extern "C" lhmm_status lhmm_micro_create(const lhmm_dpd_params* params,
     return LHMM_ERR_ARG;
   const bool planar = p.dim == 2;
   const int nb = batch->n_boxes;
+  if (batch->box_id_offset < 0) return LHMM_ERR_ARG;
   if (nb > 0 && (!batch->box_edge || !batch->n_beads || !batch->n_chains)) return LHMM_ERR_ARG;
   std::vector<BoxInfo> info(nb);
   long long total = 0;
@@ -1316,6 +1320,7 @@ extern "C" lhmm_status lhmm_micro_create(const lhmm_dpd_params* params,
   lhmm_micro_s* h = new lhmm_micro_s();
   h->p = p;
   h->n_boxes = nb;
+  h->id_base = batch->box_id_offset;
   h->chain_len = batch->chain_len;
   h->max_beads = max_beads;
   h->max_cells = max_cells;

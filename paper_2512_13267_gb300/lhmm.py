@@ -40,7 +40,7 @@ class DpdParams(C.Structure):
 class BatchDesc(C.Structure):
     _fields_ = [("n_boxes", C.c_int), ("box_edge", C.POINTER(C.c_float)),
                 ("n_beads", C.POINTER(C.c_int)), ("n_chains", C.POINTER(C.c_int)),
-                ("chain_len", C.c_int)]
+                ("chain_len", C.c_int), ("box_id_offset", C.c_int)]
 
 
 class SphParams(C.Structure):
@@ -176,7 +176,7 @@ class Micro:
     """A batch of DPD/FENE micro-domains resident on the GPU (lhmm_micro_*)."""
 
     def __init__(self, params, edges, n_beads, n_chains, chain_len, pos0, vel0, L0=None,
-                 stream=None):
+                 stream=None, box_id_offset=0):
         L = lib()
         edges, pe = _np(np.asarray(edges, np.float32).reshape(-1, 3), np.float32)
         nb, pn = _np(n_beads, np.int32)
@@ -190,16 +190,16 @@ class Micro:
         pL = None
         if L0 is not None:
             L0, pL = _np(np.asarray(L0, np.float32).reshape(self.n_boxes, 9), np.float32)
-        desc = BatchDesc(self.n_boxes, pe, pn, pc, int(chain_len))
+        desc = BatchDesc(self.n_boxes, pe, pn, pc, int(chain_len), int(box_id_offset))
         h = C.c_void_p()
         check(L.lhmm_micro_create(C.byref(params), C.byref(desc), pp, pv, pL, _stream_ptr(stream),
                                   C.byref(h)), "lhmm_micro_create")
         self.h = h
 
     @classmethod
-    def from_batch(cls, params, batch, stream=None):
+    def from_batch(cls, params, batch, stream=None, box_id_offset=0):
         return cls(params, batch.edges, batch.n_beads, batch.n_chains, batch.chain_len,
-                   batch.pos, batch.vel, L0=batch.L, stream=stream)
+                   batch.pos, batch.vel, L0=batch.L, stream=stream, box_id_offset=box_id_offset)
 
     def close(self):
         if getattr(self, "h", None):

@@ -139,6 +139,16 @@ class BoxBatch:
         o = self.offsets
         return slice(int(o[b]), int(o[b + 1]))
 
+    def boxes(self, lo, hi):
+        """The sub-batch of boxes lo .. hi-1 (one rank's share)."""
+        o = self.offsets
+        beads = slice(int(o[lo]), int(o[hi]))
+        return BoxBatch(self.edges[lo:hi].copy(), self.n_beads[lo:hi].copy(),
+                        self.n_chains[lo:hi].copy(), self.chain_len, self.L[lo:hi].copy(),
+                        None if self.pos is None else self.pos[beads].copy(),
+                        None if self.vel is None else self.vel[beads].copy(),
+                        self.flow, self.seed, self.dim)
+
 
 def make_batch(edges, L, seed, flow="afbc", chain_len=CHAIN_LEN, fraction=POLYMER_FRACTION,
                density=DENSITY, n_beads=None, kBT=1.0, with_state=True, dim=3):
