@@ -390,6 +390,8 @@ def main():
     ap.add_argument("--no-macro", action="store_true", help="skip the coupled macro-step line")
     ap.add_argument("--no-surrogate", action="store_true",
                     help="skip the surrogate-gated vs plain comparison")
+    ap.add_argument("--no-large-mixed", action="store_true",
+                    help="skip the large mixed run (cylinder array, 16.4 M beads, gated)")
     ap.add_argument("--uniform-edge", type=float, default=0.0,
                     help="give every box this edge (a one-class case for profilers)")
     ap.add_argument("--profile-case", choices=sorted(PROFILE_CASES),
@@ -564,6 +566,14 @@ def main():
                        "AdamW steps; full budget: closure.surrogate_vs_plain(n_data=500, "
                        "train_steps=20000)")
         line["surrogate"] = r
+    if rank == 0 and not args.no_large_mixed and args.uniform_edge <= 0:
+        # the large mixed run: periodic cylinder array, 16 384 fluid + wall
+        # particles, 1000-bead boxes (16.4 M beads), graph-captured macro
+        # steps, autotuned size classes, 200 plain and 200 gated macro steps
+        from paper_2512_13267_gb300 import closure
+        r = closure.large_mixed_run(timing_steps=200, seed=5)
+        r["metric"] = "LHMM macro-steps/s, large mixed run, surrogate-gated vs plain"
+        line["large_mixed"] = r
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

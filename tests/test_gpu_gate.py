@@ -176,3 +176,17 @@ def test_onpolicy_labels_are_the_dpd_stress_when_every_box_runs_dpd():
     assert np.abs(T[-n:] - ref).max() <= 1e-5 * (1.0 + np.abs(ref).max())
     for o in (shadow, cpl, clo):
         o.close()
+
+
+def test_large_mixed_run_small_cylinder_cell_gated_step():
+    # the large mixed run's pipeline (cylinder array with wall particles, one
+    # box per fluid particle, autotuned launches, pairs, training, gated
+    # graph-replayed macro steps) at a small size: it runs, the walls carry
+    # no box, the device reports no fault and the gated share is a fraction
+    from paper_2512_13267_gb300 import closure
+    out = closure.large_mixed_run(n_fluid=256, cell=4.0, box_beads=375, warm=2, n_data=20,
+                                  train_steps=40, timing_steps=3, threshold=0.02, audit_every=5)
+    assert out["device_status"] == "ok"
+    assert out["macro_steps_per_s_plain"] > 0 and out["macro_steps_per_s_surrogate"] > 0
+    assert 0.0 <= out["dpd_fraction"] <= 1.0
+    assert "wall SPH" in out["workload"] and out["train_pairs"] > 0

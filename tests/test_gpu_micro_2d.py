@@ -183,3 +183,58 @@ def test_2d_afbc_peculiar_mode_matches_oracle(parity_report):
         _, vel, _, _, _ = m.get_state(b)
         assert np.all(vel[:, 2] == 0.0)
     m.close()
+
+
+def _run_schedule(m, op, boxes, batch, schedule, parity_report, name):
+    # each (L, steps) of the schedule advances both sides; positions after
+    # every segment within 1e-3, the segment's stress average within 3 SEs
+    # of the oracle's per-step samples
+    w_pos, w_se = 0.0, 0.0
+    for Lseg, steps in schedule:
+        Ld = torch.from_numpy(np.ascontiguousarray(Lseg, np.float32)).cuda()
+        st = torch.zeros((batch.n_boxes, 6), dtype=torch.float64, device="cuda")
+        m.advance(Ld, steps, st)
+        m.sync()
+        got = st.cpu().numpy()
+        for b, ob in enumerate(boxes):
+            ref, ref_sq, err = O.advance(op, ob, Lseg[b], steps)
+            assert err == 0
+            pos = m.get_state(b)[0]
+            dpos = np.abs(_minimage(pos - ob.pos, batch.edges[b][0])).max()
+            assert dpos <= 1e-3, (name, b, dpos)
+            se = np.sqrt(np.maximum(ref_sq - ref * ref, 0.0) / steps)
+            d = np.abs(got[b] - ref)
+            assert np.all(d <= 3 * se + 1e-12 * (1 + np.abs(ref))), (name, b, got[b], ref, se)
+            w_pos = max(w_pos, dpos)
+            w_se = max(w_se, float(np.max(np.where(se > 0, d / np.where(se > 0, se, 1), 0))))
+    parity_report(name + ", positions", w_pos, 1e-3, "max |dr|")
+    parity_report(name + ", stress average", w_se, 3.0, "max |dpi| / SE")
+
+
+def test_2d_stress_relaxation_step_change_matches_oracle(parity_report):
+    # the recovery test's schedule (Sec. 5.2): Lees-Edwards shear, then the
+    # shear removed (L = 0) while the stress relaxes, then sheared again at
+    # another rate; every change of L lands between calls as in the rheometer
+    batch = _batch("lees_edwards", 31)
+    m, op, boxes = _pair(batch, "lees_edwards", 31)
+    L1 = batch.L.copy()
+    L0 = np.zeros_like(L1)
+    L2 = L1.copy()
+    L2[:, 1] *= -0.5
+    _run_schedule(m, op, boxes, batch, [(L1, 20), (L0, 15), (L2, 15)], parity_report,
+                  "2D shear - rest - reversed shear (Lees-Edwards)")
+    m.close()
+
+
+def test_2d_planar_extension_matches_oracle(parity_report):
+    # steady planar extension L = diag(e, -e) through the AFBC shell (the
+    # rheometer of rheometry.planar_extension), then the flow stopped
+    batch = _batch("afbc", 37)
+    e = np.array([0.05, 0.1, 0.2, 0.3, 0.5], np.float32)
+    L = np.zeros((batch.n_boxes, 9), np.float32)
+    L[:, 0], L[:, 4] = e, -e
+    batch.L[:] = L
+    m, op, boxes = _pair(batch, "afbc", 37)
+    _run_schedule(m, op, boxes, batch, [(L, 25), (np.zeros_like(L), 15)], parity_report,
+                  "2D planar extension - rest (AFBC)")
+    m.close()
