@@ -219,3 +219,40 @@ def planar_extension(chain_len, rates, replicas=32, edge=36.0, equil_time=None,
         psi1 = (mean[:, :, 0] - mean[:, :, 1]) / rates[:, None] ** 2
         out.update(psi1=psi1.mean(axis=1).tolist(), psi1_se=se(psi1))
     return out
+
+
+def relaxation_time(t, g, g_se, t_min=0.0, snr=3.0):
+    """Relaxation time of a stress decay g(t) after the flow stops (g = G(t)
+    or pi_xy(t); only its shape matters), from the samples with t >= t_min
+    that stand snr standard errors above zero:
+      lam_tail  = -1 / slope of a weighted straight-line fit of log g on t
+                  (the terminal, longest relaxation time);
+      lam_moment = int t g dt / int g dt over the same samples (the mean
+                  relaxation time of the decay; a single exponential gives
+                  its time constant, exactly as the window grows).
+    Returns dict(lam_tail, lam_tail_se, lam_moment, n_points, t_max)."""
+    t = np.asarray(t, np.float64)
+    g = np.asarray(g, np.float64)
+    se = np.maximum(np.asarray(g_se, np.float64), 1e-300)
+    keep = (t >= t_min) & (g > snr * se)
+    # the usable decay ends at the first sample that drops into the noise
+    idx = np.flatnonzero(t >= t_min)
+    end = idx[0] if idx.size else len(t)
+    while end < len(t) and g[end] > snr * se[end]:
+        end += 1
+    keep &= np.arange(len(t)) < end
+    tt, gg, ss = t[keep], g[keep], se[keep]
+    if tt.size < 3:
+        return dict(lam_tail=float("nan"), lam_tail_se=float("nan"),
+                    lam_moment=float("nan"), n_points=int(tt.size), t_max=float("nan"))
+    w = (gg / ss) ** 2  # var(log g) ~ (se / g)^2
+    A = np.stack([np.ones_like(tt), tt], axis=1)
+    cov = np.linalg.inv(A.T @ (A * w[:, None]))
+    coef = cov @ (A.T @ (w * np.log(gg)))
+    slope, slope_se = coef[1], np.sqrt(cov[1, 1])
+    lam = -1.0 / slope if slope < 0 else float("inf")
+    lam_se = slope_se / slope ** 2 if slope < 0 else float("inf")
+    num = np.trapezoid(tt * gg, tt)
+    den = np.trapezoid(gg, tt)
+    return dict(lam_tail=float(lam), lam_tail_se=float(lam_se),
+                lam_moment=float(num / den - tt[0]), n_points=int(tt.size), t_max=float(tt[-1]))

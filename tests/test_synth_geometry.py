@@ -49,3 +49,22 @@ def test_carreau_yasuda_fit_recovers_known_parameters():
     # a Newtonian plateau is a flat fit
     flat = R.fit_carreau_yasuda(g, np.full(8, 5.0))
     assert abs(flat["eta0"] - 5.0) < 0.05 and abs(R.carreau_yasuda(0.1, flat["eta0"], flat["eta_inf"], flat["lam"], flat["a"], flat["n"]) - 5.0) < 0.05
+
+
+def test_relaxation_time_from_decay():
+    # a fast (0.3) plus a slow (50) exponential mode with noise: the tail fit
+    # past the fast decay finds the slow time constant; a single exponential
+    # gives its time constant to both estimators; samples in the noise are
+    # left out
+    from paper_2512_13267_gb300 import rheometry as R
+    rng = np.random.default_rng(3)
+    t = np.arange(0.5, 400.0, 1.0)
+    se = np.full_like(t, 2e-3)
+    g = 0.8 * np.exp(-t / 0.3) + 0.2 * np.exp(-t / 50.0) + rng.normal(scale=2e-3, size=t.size)
+    r = R.relaxation_time(t, g, se, t_min=5.0)
+    assert abs(r["lam_tail"] - 50.0) < 3 * r["lam_tail_se"] + 1.0, r
+    assert r["t_max"] < 260  # stops where g falls into the noise (0.2 e^{-t/50} = 6e-3 near 170)
+    one = R.relaxation_time(t, np.exp(-t / 20.0), np.full_like(t, 1e-7))
+    assert abs(one["lam_tail"] - 20.0) < 1e-6 and abs(one["lam_moment"] - 20.0) < 0.05
+    flat = R.relaxation_time(t, np.full_like(t, 1e-4), np.full_like(t, 1e-3))
+    assert np.isnan(flat["lam_tail"])
