@@ -191,7 +191,8 @@ def surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, batch=4096, n_eval
                        U_o=0.25, c_factor=10.0, eta_s=0.1, k_micro=50, dt_dpd=0.01, members=5,
                        lr=1e-3, weight_decay=1e-4, cosine=False, nbins=16, thresholds=None,
                        noise_floor=False, absolute=False, warmup_steps=-1, calibrated=False,
-                       onpolicy_rounds=0, onpolicy_steps=50, onpolicy_train_steps=None):
+                       onpolicy_rounds=0, onpolicy_steps=50, onpolicy_train_steps=None,
+                       online_calibration=False, calibration_decay=0.9):
     """Plain LHMM vs surrogate-gated LHMM on the coupled reverse-Poiseuille
     channel.  Two identical systems run the same `warm + n_data` plain steps
     (one collects training pairs); the ensemble trains on the GPU; then both run
@@ -207,7 +208,10 @@ def surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, batch=4096, n_eval
     rounds of `onpolicy_steps` gated steps whose shadow-DPD labels
     (`onpolicy_pairs`) join the training set before the closure trains
     again (onpolicy_train_steps, default train_steps) and, if `calibrated`,
-    is recalibrated on the newest on-policy pairs."""
+    is recalibrated on the newest on-policy pairs.  `online_calibration`
+    lets the gate refit a per-component line from its audited boxes after
+    every gated macro step (lhmm_coupled_set_online_calibration, decay
+    `calibration_decay`) and applies it to the trusted boxes."""
     kw = dict(alpha=alpha, U_o=U_o, c_factor=c_factor, eta_s=eta_s, k_micro=k_micro,
               dt_dpd=dt_dpd, members=members)
     A, clo_a, cfg, M = _channel(seed=seed, closure_seed=1, **kw)
@@ -237,6 +241,8 @@ def surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, batch=4096, n_eval
     if calibrated:
         a_c, c_c = calibrate(clo_b, X[n_fit:], T[n_fit:], scale)
         calib = dict(a=a_c.tolist(), c=c_c.tolist())
+    if online_calibration:
+        B.set_online_calibration(True, calibration_decay)
     B.enable_gate(True)
     n_onpolicy = 0
     if onpolicy_rounds > 0:
@@ -305,6 +311,7 @@ def surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, batch=4096, n_eval
         t_data_s=t_data, t_train_s=t_train, sph_substeps=M, micro_steps=k_micro,
         boxes=B.n_boxes, threshold=last["threshold"], audit_every=audit_every, n_eval=n_eval,
         target="stress" if absolute else "increment", calibration=calib,
+        online_calibration=(B.set_online_calibration(-1).tolist() if online_calibration else None),
         windows=windows if len(windows) > 1 else None,
         noise_floor_pxy=last.get("noise_floor_pxy"), noise_floor_n1=last.get("noise_floor_n1"),
         profile_pxy_plain=last["profile_pxy_plain"],
