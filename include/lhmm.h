@@ -431,6 +431,18 @@ lhmm_status lhmm_coupled_enable_gate(lhmm_coupled_t c, int enabled);
  * macro step re-captures its graph.  Synchronous. */
 lhmm_status lhmm_coupled_set_gate(lhmm_coupled_t c, float threshold, int audit_every,
                                   int absolute, int warmup_steps);
+/* Online calibration of the closure from its audits (not in the paper).  The
+ * audited boxes run DPD anyway; after each gated macro step their raw
+ * predictions p and DPD values d (per component: the stress in the absolute
+ * mode, its increment otherwise) join decayed sums (older steps weighted by
+ * decay^age) and a least-squares line d = a p + c is refitted per component
+ * (a held to [1/4, 4]; the identity until 20 weighted audits have been
+ * seen).  enabled = 1: trusted boxes take a p + c instead of p; 0: they take
+ * p (the sums are still kept); -1: change nothing.  decay in (0, 1].
+ * map_host (6 floats, or NULL) receives the current (a, c) of xx, xy, yy.
+ * The next macro step re-captures its graph.  Synchronous. */
+lhmm_status lhmm_coupled_set_online_calibration(lhmm_coupled_t c, int enabled, float decay,
+                                                float* map_host);
 /* Counters since the closure was attached: gated macro steps, boxes advanced
  * by DPD in them, audited boxes, and over the audited boxes the summed squared
  * error of the predicted increment and the summed squared DPD increment.

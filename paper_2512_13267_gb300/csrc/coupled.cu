@@ -38,6 +38,13 @@ struct GateState {
   int* resume = nullptr;    // n box list of frozen boxes that run DPD this step
   int* n_resume = nullptr;  // device count of that list
   double* scratch = nullptr;  // n x 6 stress output of the warm-up (discarded)
+  // online calibration: trusted boxes take a_k pred_k + c_k per component k,
+  // (a, c) the least-squares line of the audited boxes' DPD values on their
+  // raw predictions, older macro steps' audits weighted by cal_decay^age
+  int online = 0;
+  float cal_decay = 0.9f;
+  double* cal = nullptr;    // [0..14] decayed sums (n, p, d, pp, pd) x 3; [15..29] this step's
+  float* cal_map = nullptr; // (a, c) x 3, read by gate_select
 };
 
 struct lhmm_coupled_s {
@@ -89,7 +96,8 @@ __global__ void gate_select(const float* mean, const float* spread, double* stre
                             float thr, float floor_, int audit_every, int absolute,
                             long long* counters, int* active, int* n_active,
                             unsigned char* audited, float* pred, float* before,
-                            unsigned char* frozen, int* resume, int* n_resume) {
+                            unsigned char* frozen, int* resume, int* n_resume,
+                            const float* cal_map) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= n) return;
   double* s = stress + 6 * static_cast<long long>(I);
@@ -118,9 +126,9 @@ __global__ void gate_select(const float* mean, const float* spread, double* stre
     }
   } else {
     frozen[I] = 1;
-    s[0] = static_cast<double>(bxx) + dxx;
-    s[3] = static_cast<double>(bxy) + dxy;
-    s[1] = static_cast<double>(byy) + dyy;
+    s[0] = static_cast<double>(bxx) + (cal_map[0] * dxx + cal_map[1]);
+    s[3] = static_cast<double>(bxy) + (cal_map[2] * dxy + cal_map[3]);
+    s[1] = static_cast<double>(byy) + (cal_map[4] * dyy + cal_map[5]);
   }
 }
 
@@ -130,7 +138,7 @@ __global__ void gate_tally(long long* counters, const int* n_active) {
 }
 
 __global__ void gate_audit(const double* stress, int n, unsigned char* audited, const float* pred,
-                           const float* before, long long* counters, double* audit) {
+                           const float* before, long long* counters, double* audit, double* cal) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= n || !audited[I]) return;
   audited[I] = 0;
@@ -140,6 +148,44 @@ __global__ void gate_audit(const double* stress, int n, unsigned char* audited, 
   atomicAdd(&audit[0], e0 * e0 + e1 * e1 + e2 * e2);
   atomicAdd(&audit[1], a0 * a0 + a1 * a1 + a2 * a2);
   atomicAdd(reinterpret_cast<unsigned long long*>(&counters[2]), 1ull);
+  // this step's sums for the calibration line (raw prediction p, DPD value d)
+  const double d[3] = {a0, a1, a2};
+  double* step = cal + 15;
+  for (int k = 0; k < 3; ++k) {
+    const double p = pred[3 * I + k];
+    atomicAdd(&step[5 * k + 0], 1.0);
+    atomicAdd(&step[5 * k + 1], p);
+    atomicAdd(&step[5 * k + 2], d[k]);
+    atomicAdd(&step[5 * k + 3], p * p);
+    atomicAdd(&step[5 * k + 4], p * d[k]);
+  }
+}
+
+// fold this step's audit sums into the decayed sums and refit each
+// component's line d = a p + c (identity while off, or with fewer than 20
+// weighted audits or no spread in p); a is held to [1/4, 4]
+__global__ void gate_calibrate(double* cal, float* cal_map, float decay, int online) {
+  const int k = threadIdx.x;
+  if (k >= 3) return;
+  double* run = cal + 5 * k;
+  double* step = cal + 15 + 5 * k;
+  for (int j = 0; j < 5; ++j) {
+    run[j] = static_cast<double>(decay) * run[j] + step[j];
+    step[j] = 0.0;
+  }
+  float a = 1.f, c = 0.f;
+  const double w = run[0];
+  if (online && w >= 20.0) {
+    const double mp = run[1] / w, md = run[2] / w;
+    const double vp = run[3] / w - mp * mp, cpd = run[4] / w - mp * md;
+    if (vp > 1e-12 * (mp * mp + 1e-30)) {
+      const double s = fmin(fmax(cpd / vp, 0.25), 4.0);
+      a = static_cast<float>(s);
+      c = static_cast<float>(md - s * mp);
+    }
+  }
+  cal_map[2 * k] = a;
+  cal_map[2 * k + 1] = c;
 }
 
 lhmm_status enqueue_macro_step(lhmm_coupled_s* c, cudaStream_t s, bool gated) {
@@ -162,7 +208,7 @@ lhmm_status enqueue_macro_step(lhmm_coupled_s* c, cudaStream_t s, bool gated) {
   LHMM_CK(cudaMemsetAsync(g.n_resume, 0, sizeof(int), s));
   gate_select<<<G, T, 0, s>>>(g.mean, g.spread, c->stress_d, n, g.threshold, g.floor, g.audit_every,
                               g.absolute, g.counters, g.active, g.n_active, g.audited, g.pred,
-                              g.before, g.frozen, g.resume, g.n_resume);
+                              g.before, g.frozen, g.resume, g.n_resume, g.cal_map);
   gate_tally<<<1, 1, 0, s>>>(g.counters, g.n_active);
   LHMM_CK(cudaGetLastError());
   const int warm = g.warmup < 0 ? c->micro_steps : g.warmup;
@@ -174,7 +220,9 @@ lhmm_status enqueue_macro_step(lhmm_coupled_s* c, cudaStream_t s, bool gated) {
   st = lhmm_micro_advance_dev_count(c->micro, c->L_d, g.active, g.n_active, n, c->micro_steps,
                                     c->stress_d, nullptr, s);
   if (st != LHMM_OK) return st;
-  gate_audit<<<G, T, 0, s>>>(c->stress_d, n, g.audited, g.pred, g.before, g.counters, g.audit);
+  gate_audit<<<G, T, 0, s>>>(c->stress_d, n, g.audited, g.pred, g.before, g.counters, g.audit,
+                             g.cal);
+  gate_calibrate<<<1, 32, 0, s>>>(g.cal, g.cal_map, g.cal_decay, g.online);
   LHMM_CK(cudaGetLastError());
   return LHMM_OK;
 }
@@ -195,6 +243,8 @@ void free_gate(GateState& g) {
   cudaFree(g.resume);
   cudaFree(g.n_resume);
   cudaFree(g.scratch);
+  cudaFree(g.cal);
+  cudaFree(g.cal_map);
   g = GateState();
 }
 
@@ -324,12 +374,20 @@ extern "C" lhmm_status lhmm_coupled_set_closure(lhmm_coupled_t c, lhmm_closure_t
       (e = cudaMalloc(&g.resume, sizeof(int) * n)) != cudaSuccess ||
       (e = cudaMalloc(&g.n_resume, sizeof(int))) != cudaSuccess ||
       (e = cudaMalloc(&g.scratch, sizeof(double) * n * 6)) != cudaSuccess ||
+      (e = cudaMalloc(&g.cal, sizeof(double) * 30)) != cudaSuccess ||
+      (e = cudaMalloc(&g.cal_map, sizeof(float) * 6)) != cudaSuccess ||
+      (e = cudaMemset(g.cal, 0, sizeof(double) * 30)) != cudaSuccess ||
       (e = cudaMemset(g.frozen, 0, n)) != cudaSuccess ||
       (e = cudaMemset(g.hist, 0, sizeof(float) * n * kHist * 4)) != cudaSuccess ||
       (e = cudaMemset(g.counters, 0, sizeof(long long) * 4)) != cudaSuccess ||
       (e = cudaMemset(g.audit, 0, sizeof(double) * 2)) != cudaSuccess ||
       (e = cudaMemset(g.audited, 0, n)) != cudaSuccess ||
       (e = cudaMemset(g.n_active, 0, sizeof(int))) != cudaSuccess) {
+    free_gate(g);
+    return lhmm_cuda_error(e);
+  }
+  const float identity[6] = {1.f, 0.f, 1.f, 0.f, 1.f, 0.f};
+  if ((e = cudaMemcpy(g.cal_map, identity, sizeof(identity), cudaMemcpyHostToDevice)) != cudaSuccess) {
     free_gate(g);
     return lhmm_cuda_error(e);
   }
@@ -352,6 +410,20 @@ extern "C" lhmm_status lhmm_coupled_set_gate(lhmm_coupled_t c, float threshold, 
   c->gate.audit_every = audit_every;
   c->gate.absolute = absolute;
   c->gate.warmup = warmup_steps;
+  return LHMM_OK;
+}
+
+extern "C" lhmm_status lhmm_coupled_set_online_calibration(lhmm_coupled_t c, int enabled,
+                                                          float decay, float* map_host) {
+  if (!c || !c->gate.closure || (enabled != 0 && enabled != 1 && enabled != -1) ||
+      !(decay > 0.f && decay <= 1.f))
+    return LHMM_ERR_ARG;
+  LHMM_CK(cudaDeviceSynchronize());
+  if (map_host) LHMM_CK(cudaMemcpy(map_host, c->gate.cal_map, sizeof(float) * 6, cudaMemcpyDeviceToHost));
+  if (enabled == -1) return LHMM_OK;  // read only
+  drop_graphs(c);  // the flag and the decay are launch arguments of a captured graph
+  c->gate.online = enabled;
+  c->gate.cal_decay = decay;
   return LHMM_OK;
 }
 

@@ -103,6 +103,7 @@ def lib():
         L.lhmm_coupled_set_closure.argtypes = [vp, vp, C.c_float, C.c_float, C.c_int]
         L.lhmm_coupled_enable_gate.argtypes = [vp, C.c_int]
         L.lhmm_coupled_set_gate.argtypes = [vp, C.c_float, C.c_int, C.c_int, C.c_int]
+        L.lhmm_coupled_set_online_calibration.argtypes = [vp, C.c_int, C.c_float, _F]
         L.lhmm_coupled_gate_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                               C.POINTER(C.c_int64), _D, _D]
         L.lhmm_coupled_closure_inputs.argtypes = [vp, _F]
@@ -404,6 +405,16 @@ class Coupled:
                                              float(stress_floor), int(audit_every)),
               "lhmm_coupled_set_closure")
         self.closure = closure
+
+    def set_online_calibration(self, enabled=True, decay=0.9):
+        """Trusted boxes take a p + c, the line fitted to the audited boxes'
+        DPD values on their raw predictions (enabled=-1 only reads the map).
+        Returns the current (a, c) of xx, xy, yy as a 3 x 2 array."""
+        m = np.zeros(6, np.float32)
+        check(lib().lhmm_coupled_set_online_calibration(self.h, int(enabled), float(decay),
+                                                        m.ctypes.data_as(_F)),
+              "lhmm_coupled_set_online_calibration")
+        return m.reshape(3, 2)
 
     def enable_gate(self, on=True):
         check(lib().lhmm_coupled_enable_gate(self.h, int(bool(on))), "lhmm_coupled_enable_gate")

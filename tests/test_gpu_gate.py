@@ -190,3 +190,43 @@ def test_large_mixed_run_small_cylinder_cell_gated_step():
     assert out["macro_steps_per_s_plain"] > 0 and out["macro_steps_per_s_surrogate"] > 0
     assert 0.0 <= out["dpd_fraction"] <= 1.0
     assert "wall SPH" in out["workload"] and out["train_pairs"] > 0
+
+
+def test_online_calibration_fits_the_audits():
+    # every trusted box audited (audit_every = 1): all boxes run DPD, so two
+    # systems whose closures differ only by a shifted output bias (every
+    # member's prediction moved by delta, the ensemble spread unchanged) see
+    # the same flow, and the fitted lines must be a' = a, c' = c - a delta
+    # (whatever a is, also where it is held at a bound); with the calibration
+    # off the map stays the identity
+    delta_n, out_scale = 2.0, 1e-3  # shift in normalised output units; _system's output scale
+    systems = []
+    for shift in (False, True):
+        cpl, clo = _system(seed=19)
+        if shift:
+            for m in range(5):
+                p = clo.get_params(m)
+                p[-3:] += delta_n  # b of the output layer
+                clo.set_params(m, p)
+        cpl.set_closure(clo, threshold=1e30, audit_every=1)
+        cpl.step(17, use_graph=True)
+        cpl.set_online_calibration(True, decay=0.8)
+        cpl.enable_gate(True)
+        cpl.step(5, use_graph=True)
+        systems.append((cpl, clo))
+    (a, _), (b, _) = systems
+    La, sa = a.exchange()
+    Lb, sb = b.exchange()
+    assert np.array_equal(La, Lb) and np.array_equal(sa, sb)
+    ma = a.set_online_calibration(-1)
+    mb = b.set_online_calibration(-1)
+    assert not np.allclose(ma, [[1, 0], [1, 0], [1, 0]])
+    assert np.allclose(mb[:, 0], ma[:, 0], rtol=1e-4), (ma, mb)
+    shift = ma[:, 0] * delta_n * out_scale
+    assert np.allclose(mb[:, 1], ma[:, 1] - shift, rtol=0, atol=1e-3 * np.abs(shift).max()), (ma, mb)
+    c, cc = _system(seed=19)
+    c.set_closure(cc, threshold=1e30, audit_every=1)
+    c.step(17, use_graph=True)
+    c.enable_gate(True)
+    c.step(3, use_graph=True)
+    assert np.array_equal(c.set_online_calibration(-1), [[1, 0], [1, 0], [1, 0]])
