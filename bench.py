@@ -558,12 +558,14 @@ def main():
     if rank == 0 and not args.no_surrogate and args.uniform_edge <= 0:
         from paper_2512_13267_gb300 import closure
         r = closure.surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, n_eval=60,
-                                       absolute=True, calibrated=True, weight_decay=0.0)
+                                       absolute=True, calibrated=True, weight_decay=0.0,
+                                       threshold=0.05, online_calibration=True, noise_floor=True)
         for k in ("profile_pxy_plain", "profile_pxy_surrogate"):
             r.pop(k, None)
         r["metric"] = "LHMM macro-steps/s, surrogate-gated vs plain"
         r["budget"] = ("bench budget: 150 macro steps of training pairs (307k pairs), 2000 "
-                       "AdamW steps; full budget: closure.surrogate_vs_plain(n_data=500, "
+                       "AdamW steps, gate threshold 0.05 with online calibration from the "
+                       "audits; full budget: closure.surrogate_vs_plain(n_data=500, "
                        "train_steps=20000)")
         line["surrogate"] = r
     if rank == 0 and not args.no_large_mixed and args.uniform_edge <= 0:

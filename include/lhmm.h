@@ -225,7 +225,12 @@ lhmm_status lhmm_micro_info(lhmm_micro_t h, int* n_boxes, int64_t* total_beads, 
 
 /* Time every variant on probe_steps steps of each class's boxes under L_dev
  * (device, n_boxes x 9) and keep the fastest per class; results are cached
- * per (largest box, cells, flow mode, device) for the process.  The bead state
+ * per (largest box, cells, flow mode, device) for the process.  Then the
+ * tuned class plan is timed against one persistent launch over every box
+ * (a grid of resident blocks pulling box ids, largest box first, from a
+ * device counter) in each variant that holds the largest box, and full
+ * advances (box_idx_dev == NULL) use the faster (lhmm_micro_plan then reports
+ * the persistent launch as one class).  The bead state
  * is saved before and restored after, so the batch does not advance.  The
  * choice changes floating-point summation order, so a run is bit-reproducible
  * for a fixed plan (see lhmm_micro_set_variant).  Synchronous; allocates a
@@ -237,7 +242,8 @@ lhmm_status lhmm_micro_autotune(lhmm_micro_t h, const float* L_dev, int probe_st
 lhmm_status lhmm_micro_plan(lhmm_micro_t h, int* n_classes, int cap, int* class_boxes,
                             int* class_max_beads, int* class_threads, int* class_min_blocks);
 
-/* Pin the kernel variant (0..LHMM_MICRO_N_VARIANTS-1) of one class.  Returns
+/* Pin the kernel variant (0..LHMM_MICRO_N_VARIANTS-1) of one class (this
+ * returns full advances to the class plan).  Returns
  * LHMM_ERR_UNSUPPORTED if that variant's shared-memory plan does not fit.
  * Pinning a device-memory variant (5, 6) may allocate the scratch buffer:
  * call it before capturing advances into a CUDA graph. */

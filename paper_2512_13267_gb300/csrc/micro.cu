@@ -1088,6 +1088,9 @@ struct lhmm_micro_s {
   std::vector<SizeClass> classes;
   cudaEvent_t fork = nullptr;
   int* work_counter = nullptr;  // persistent-mode item counter
+  bool all_persistent = false;  // full advances as one persistent launch (autotuner's choice)
+  int all_variant = 0;          // its kernel variant
+  int* n_all_d = nullptr;       // device copy of n_boxes, its item count
   int subset_variant = 1;  // single launch over a device-side box list
   unsigned char* gm = nullptr;  // per-box scratch of the global-memory variants
   size_t gm_stride = 0;
@@ -1184,6 +1187,7 @@ void free_micro(lhmm_micro_t h) {
   }
   if (h->fork) cudaEventDestroy(h->fork);
   cudaFree(h->work_counter);
+  cudaFree(h->n_all_d);
   cudaFree(h->gm);
   delete h;
 }
@@ -1244,6 +1248,26 @@ cudaError_t launch_classes(lhmm_micro_s* h, MicroArgs a, cudaStream_t s) {
     if ((e = cudaStreamWaitEvent(s, c.done, 0)) != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// Every box in one persistent launch: a grid of the variant's resident blocks
+// on every SM pulls box ids, largest box first, from a device counter.
+cudaError_t launch_all_persistent(lhmm_micro_s* h, MicroArgs a, cudaStream_t s) {
+  int dev = 0, n_sm = 0;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return e;
+  const int v = h->all_variant;
+  a.list = h->order_d;
+  a.max_beads = h->max_beads;
+  a.max_cells = h->max_cells;
+  a.work_counter = h->work_counter;
+  a.n_items_dev = h->n_all_d;
+  a.max_items = h->n_boxes;
+  const int grid = std::min(h->n_boxes, kVariants[v].min_blocks * n_sm);
+  if ((e = cudaMemsetAsync(h->work_counter, 0, sizeof(int), s)) != cudaSuccess) return e;
+  return launch_variant(v, a, grid, class_smem(h->max_beads, h->max_cells, v), s);
 }
 
 cudaError_t launch_subset(lhmm_micro_s* h, MicroArgs a, const int* list, int n, cudaStream_t s) {
@@ -1383,7 +1407,9 @@ extern "C" lhmm_status lhmm_micro_create(const lhmm_dpd_params* params,
       (e = cudaMalloc(&h->st_stage, sizeof(double) * 6 * nbx)) != cudaSuccess ||
       (e = cudaMalloc(&h->sq_stage, sizeof(double) * 6 * nbx)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming)) != cudaSuccess ||
-      (e = cudaMalloc(&h->work_counter, sizeof(int))) != cudaSuccess)
+      (e = cudaMalloc(&h->work_counter, sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&h->n_all_d, sizeof(int))) != cudaSuccess ||
+      (e = cudaMemcpy(h->n_all_d, &nb, sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
     return fail(lhmm_cuda_error(e));
   if (kVariants[h->subset_variant].gm && (e = ensure_gm(h)) != cudaSuccess)
     return fail(lhmm_cuda_error(e));
@@ -1458,6 +1484,8 @@ extern "C" lhmm_status lhmm_micro_advance(lhmm_micro_t h, const float* L_dev,
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (box_idx_dev) {
     LHMM_CK(launch_subset(h, a, box_idx_dev, n_active, s));
+  } else if (h->all_persistent) {
+    LHMM_CK(launch_all_persistent(h, a, s));
   } else {
     LHMM_CK(launch_classes(h, a, s));
   }
@@ -1653,6 +1681,7 @@ extern "C" lhmm_status lhmm_micro_autotune(lhmm_micro_t h, const float* L_dev, i
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   lhmm_status result = LHMM_OK;
+  int tuned_all = 0;
   for (auto& c : h->classes) {
     const auto key = std::make_tuple(c.max_beads, c.max_cells, h->p.flow_mode, dev);
     {
@@ -1694,6 +1723,39 @@ extern "C" lhmm_status lhmm_micro_autotune(lhmm_micro_t h, const float* L_dev, i
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = best_v;
   }
+  // the whole batch: the tuned class plan against one persistent launch over
+  // every box (largest first) in each variant that holds the largest box
+  h->all_persistent = false;
+  if (result == LHMM_OK && h->classes.size() > 1) {
+    auto time_it = [&](auto launch, float& ms) -> cudaError_t {
+      cudaError_t x;
+      if ((x = launch()) != cudaSuccess || (x = cudaEventRecord(e0, s)) != cudaSuccess ||
+          (x = launch()) != cudaSuccess || (x = cudaEventRecord(e1, s)) != cudaSuccess ||
+          (x = cudaEventSynchronize(e1)) != cudaSuccess)
+        return x;
+      return cudaEventElapsedTime(&ms, e0, e1);
+    };
+    float best = 1e30f;
+    e = time_it([&]() { return launch_classes(h, a, s); }, best);
+    const bool big = !fits_shared(h->max_beads, h->max_cells, optin);
+    for (int v = 0; v < kNumVariants && e == cudaSuccess; ++v) {
+      if (class_smem(h->max_beads, h->max_cells, v) > optin || kVariants[v].gm != big) continue;
+      if (kVariants[v].gm && (e = ensure_gm(h)) != cudaSuccess) break;
+      h->all_variant = v;
+      float ms = 0.f;
+      if ((e = time_it([&]() { return launch_all_persistent(h, a, s); }, ms)) != cudaSuccess) break;
+      if (ms < best) {
+        best = ms;
+        h->all_persistent = true;
+        tuned_all = v;
+      }
+    }
+    if (e != cudaSuccess) {
+      result = lhmm_cuda_error(e);
+      h->all_persistent = false;
+    }
+    if (h->all_persistent) h->all_variant = tuned_all;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   // restore the state the probes advanced
@@ -1712,6 +1774,16 @@ extern "C" lhmm_status lhmm_micro_plan(lhmm_micro_t h, int* n_classes, int cap, 
                                        int* class_max_beads, int* class_threads,
                                        int* class_min_blocks) {
   if (!h || !n_classes) return LHMM_ERR_ARG;
+  if (h->all_persistent) {  // one launch over every box
+    *n_classes = 1;
+    if (cap > 0) {
+      if (class_boxes) class_boxes[0] = h->n_boxes;
+      if (class_max_beads) class_max_beads[0] = h->max_beads;
+      if (class_threads) class_threads[0] = kVariants[h->all_variant].threads;
+      if (class_min_blocks) class_min_blocks[0] = kVariants[h->all_variant].min_blocks;
+    }
+    return LHMM_OK;
+  }
   *n_classes = static_cast<int>(h->classes.size());
   for (int k = 0; k < cap && k < *n_classes; ++k) {
     const SizeClass& c = h->classes[k];
@@ -1730,5 +1802,6 @@ extern "C" lhmm_status lhmm_micro_set_variant(lhmm_micro_t h, int cls, int varia
   if (class_smem(c.max_beads, c.max_cells, variant) > max_optin_smem()) return LHMM_ERR_UNSUPPORTED;
   if (kVariants[variant].gm) LHMM_CK(ensure_gm(h));
   c.variant = variant;
+  h->all_persistent = false;  // an explicit class variant means the class plan
   return LHMM_OK;
 }

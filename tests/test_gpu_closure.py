@@ -136,8 +136,17 @@ def test_calibration_folds_linear_map_into_output_layer():
     Xd = torch.from_numpy(X).cuda()
     P = c.forward_members(Xd).mean(axis=0) * scale
     T = (np.array([1.5, -0.7, 2.0]) * P + np.array([0.3, 0.1, -0.2])).astype(np.float32)
+    before = [c.get_params(m).astype(np.float64) for m in range(3)]
     a, b = CL.calibrate(c, X, T, scale)
     assert np.allclose(a, [1.5, -0.7, 2.0], rtol=1e-3) and np.allclose(b, [0.3, 0.1, -0.2], atol=1e-3)
+    # the fold through the FP64 oracle network: every member's folded output
+    # is a y + c / scale of its output before (the map is linear in the last
+    # layer, so this holds to the FP32 rounding of the stored parameters)
+    Xs = X[:64].astype(np.float64)
+    for m in range(3):
+        y0 = O.mlp_forward(DIMS, before[m], Xs)
+        y1 = O.mlp_forward(DIMS, c.get_params(m).astype(np.float64), Xs)
+        assert np.allclose(y1, a * y0 + b / scale, rtol=1e-5, atol=1e-6 * np.abs(y0).max())
     mean = torch.zeros((512, 3), dtype=torch.float32, device="cuda")
     spread = torch.zeros(512, dtype=torch.float32, device="cuda")
     c.infer(Xd, mean, spread)

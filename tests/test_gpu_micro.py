@@ -450,3 +450,35 @@ def test_one_call_of_k_steps_equals_k_calls_of_one_step(flow, afbc_mode):
             assert np.array_equal(np.asarray(x), np.asarray(y)), box
     a.close()
     b.close()
+
+
+def test_full_advance_plan_chosen_by_autotune_gives_the_variants_results():
+    # the autotuner may replace the size-class launches by one persistent
+    # launch over every box (largest first) in one variant; a box's result
+    # depends only on the variant that runs it, so a handle with every class
+    # pinned to the chosen variants reproduces it bit for bit
+    lh = _lh()
+    batch = S.batched_microsolver(n_boxes=96, seed=23)
+    L = torch.from_numpy(batch.L).cuda()
+    a = lh.Micro.from_batch(lh.dpd_params(flow="afbc", seed=23), batch)
+    b = lh.Micro.from_batch(lh.dpd_params(flow="afbc", seed=23), batch)
+    a.autotune(L, probe_steps=3)
+    plan = a.plan()
+    variants = {(t, mb): k for k, (t, mb, gm) in enumerate(lh.MICRO_VARIANTS) if not gm}
+    n_cls = len(b.plan())
+    if len(plan) == 1 and n_cls > 1:  # one persistent launch
+        for c in range(n_cls):
+            b.set_variant(c, variants[(plan[0]["threads"], plan[0]["min_blocks"])])
+    else:
+        for c, p in enumerate(plan):
+            b.set_variant(c, variants[(p["threads"], p["min_blocks"])])
+    sa = torch.zeros((batch.n_boxes, 6), dtype=torch.float64, device="cuda")
+    sb = torch.zeros_like(sa)
+    a.advance(L, 10, sa)
+    b.advance(L, 10, sb)
+    assert np.array_equal(sa.cpu().numpy(), sb.cpu().numpy())
+    for box in (0, 17, 95):
+        for x, y in zip(a.get_state(box)[:4], b.get_state(box)[:4]):
+            assert np.array_equal(np.asarray(x), np.asarray(y))
+    a.close()
+    b.close()
