@@ -55,10 +55,10 @@ ALGO_OPS_PER_BEAD_STEP = PAIRS_PER_BEAD * (FP32_PER_PAIR + INT_PER_PAIR + SFU_PE
 ISSUED_OPS_PER_BEAD_STEP = PAIRS_PER_BEAD * 159 + 35
 LANES_PER_SM_CLK = 128  # FP32/INT32 lanes of an SM (4 sub-partitions x 32)
 # DRAM bytes (read + write) per bead and call of micro_kernel, from the ncu
-# capture in profiles/micro_kernel_e12_304box_full.md (76.02 + 16.07 MB for
+# capture in profiles/micro_kernel_e12_304box_full.md (75.84 + 16.04 MB for
 # 1,575,936 beads); the kernel reads and writes box state once per call, so
 # traffic scales with beads, not with DPD steps.
-DRAM_BYTES_PER_BEAD_CALL = 92.087e6 / 1575936
+DRAM_BYTES_PER_BEAD_CALL = 91.884e6 / 1575936
 
 
 def build_probe(force=False):
@@ -501,8 +501,8 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
                 "frac": achieved / alu_peak,
                 "traffic": DRAM_BYTES_PER_BEAD_CALL * batch.total_beads,
-                "traffic_unit": "bytes per call (all size-class launches), scaled by beads from "
-                                "the 304-box capture",
+                "traffic_unit": "bytes per call (every micro_kernel launch of the call), scaled "
+                                "by beads from the 304-box capture",
                 "peak_source": "%d SMs (queried) x %d FP32/INT lanes x %.0f MHz (%s sm_max_mhz)"
                                % (n_sm, LANES_PER_SM_CLK, clk_mhz, src),
                 "kernel": "micro_kernel", "algo_ops_per_bead_step": ALGO_OPS_PER_BEAD_STEP,
