@@ -557,16 +557,16 @@ def main():
         line["rpm_paper"] = rpm
     if rank == 0 and not args.no_surrogate and args.uniform_edge <= 0:
         from paper_2512_13267_gb300 import closure
-        r = closure.surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, n_eval=60,
+        r = closure.surrogate_vs_plain(warm=20, n_data=500, train_steps=20000, n_eval=60,
                                        absolute=True, calibrated=True, weight_decay=0.0,
-                                       threshold=0.05, online_calibration=True, noise_floor=True)
+                                       threshold=0.1, online_calibration=True, noise_floor=True)
         for k in ("profile_pxy_plain", "profile_pxy_surrogate"):
             r.pop(k, None)
         r["metric"] = "LHMM macro-steps/s, surrogate-gated vs plain"
-        r["budget"] = ("bench budget: 150 macro steps of training pairs (307k pairs), 2000 "
-                       "AdamW steps, gate threshold 0.05 with online calibration from the "
-                       "audits; full budget: closure.surrogate_vs_plain(n_data=500, "
-                       "train_steps=20000)")
+        r["budget"] = ("500 macro steps of training pairs (1.02M pairs), 20000 AdamW steps, "
+                       "stress target, held-out calibration, gate threshold 0.1 with online "
+                       "calibration from the audits (2% round-robin), warm-up k' steps for "
+                       "boxes that return to DPD")
         line["surrogate"] = r
     if rank == 0 and not args.no_large_mixed and args.uniform_edge <= 0:
         # the large mixed run: periodic cylinder array, 16 384 fluid + wall
