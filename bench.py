@@ -429,7 +429,7 @@ def main():
     stress = torch.zeros((batch.n_boxes, 6), dtype=torch.float64, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
 
-    micro.autotune(L, probe_steps=10)  # launch plan per size class (state restored)
+    micro.autotune(L, probe_steps=10)  # launch plan: size classes or one persistent launch (state restored)
     for _ in range(max(args.warmup, 0)):
         micro.advance(L, MICRO_STEPS, stress)
     torch.cuda.synchronize()
@@ -571,7 +571,7 @@ def main():
     if rank == 0 and not args.no_large_mixed and args.uniform_edge <= 0:
         # the large mixed run: periodic cylinder array, 16 384 fluid + wall
         # particles, 1000-bead boxes (16.4 M beads), graph-captured macro
-        # steps, autotuned size classes, 200 plain and 200 gated macro steps
+        # steps, autotuned launch plan, 200 plain and 200 gated macro steps
         from paper_2512_13267_gb300 import closure
         r = closure.large_mixed_run(timing_steps=200, seed=5)
         r["metric"] = "LHMM macro-steps/s, large mixed run, surrogate-gated vs plain"

@@ -429,7 +429,7 @@ def large_mixed_run(n_fluid=16384, cell=16.0, box_beads=1000, U_o=0.25, c_factor
     """Periodic array of cylinders (radius 0.25 of the cell width) with wall
     particles, one box of box_beads beads per fluid particle; plain macro
     steps, then pairs, closure training and surrogate-gated macro steps on the
-    same system (CUDA graphs, autotuned size classes, persistent gated
+    same system (CUDA graphs, the autotuned launch plan, persistent gated
     launches).  Returns rates and counts."""
     import torch
     from . import synth

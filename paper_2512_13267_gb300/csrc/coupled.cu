@@ -3,8 +3,8 @@
 // SPH velocity gradient sent down to every micro-domain, k' DPD steps of
 // every box under its gradient, and the time-averaged IK stress sent back up.
 // Exchange buffers stay on the device.  The whole macro step can be captured
-// once into a CUDA graph (including the micro engine's forked size-class
-// streams) and replayed, which removes per-kernel launch overhead from the
+// once into a CUDA graph (including the micro engine's launches: one
+// persistent launch, or size classes on forked streams) and replayed, which removes per-kernel launch overhead from the
 // ~60 small SPH launches of each interval.
 #include <vector>
 
