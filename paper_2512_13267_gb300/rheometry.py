@@ -27,40 +27,51 @@ def carreau_yasuda(gdot, eta0, eta_inf, lam, a, n):
     return eta_inf + (eta0 - eta_inf) * (1.0 + (lam * g) ** a) ** ((n - 1.0) / a)
 
 
-def fit_carreau_yasuda(gdot, eta, eta_se=None, fix_eta_inf=None):
+def fit_carreau_yasuda(gdot, eta, eta_se=None, fix_eta_inf=None, fix_a=None, fix_n=None):
     """Least-squares Carreau-Yasuda fit (Sec. 5.1, appendix on the CY model)
     of eta(gdot), in log eta with weights from the standard errors when given.
     Returns dict(eta0, eta_inf, lam, a, n, rms_log_residual).  fix_eta_inf
-    pins eta_inf (the plateau at high rates is often outside the data)."""
+    pins eta_inf (the plateau at high rates is often outside the data);
+    fix_a / fix_n pin the transition sharpness and the power-law index, so
+    that with the paper's shape parameters only eta0 and the onset time lam
+    are fitted (over two decades of rate lam otherwise trades off against
+    n and eta_inf)."""
     from scipy.optimize import least_squares
     g = np.asarray(gdot, dtype=np.float64)
     y = np.asarray(eta, dtype=np.float64)
     w = np.ones_like(y) if eta_se is None else y / np.maximum(np.asarray(eta_se, np.float64),
                                                               1e-3 * y)
     w = w / w.mean()
+    # free parameters in order: log eta0, log(lam median(g)), a, n, log(eta_inf / eta0)
+    names = ["eta0", "lam", "a", "n", "inf"]
+    fixed = {"a": fix_a, "n": fix_n, "inf": fix_eta_inf}
+    free = [k for k in names if fixed.get(k) is None]
+    q0 = {"eta0": np.log(y.max() * 1.2), "lam": 0.0, "a": 1.0, "n": 0.4, "inf": np.log(0.05)}
+    lo = {"eta0": np.log(y.max() * 0.5), "lam": np.log(1e-2 / g.max() * np.median(g)), "a": 0.2,
+          "n": 0.0, "inf": np.log(1e-4)}
+    hi = {"eta0": np.log(y.max() * 20.0), "lam": np.log(1e3 / g.min() * np.median(g)), "a": 3.0,
+          "n": 0.99, "inf": np.log(0.5)}
 
     def unpack(q):
-        eta0, lam, a, n = np.exp(q[0]), np.exp(q[1]), q[2], q[3]
-        eta_inf = fix_eta_inf if fix_eta_inf is not None else np.exp(q[4]) * eta0
+        v = dict(zip(free, q))
+        eta0 = np.exp(v["eta0"])
+        lam = np.exp(v["lam"]) / np.median(g)
+        a = v["a"] if fix_a is None else fix_a
+        n = v["n"] if fix_n is None else fix_n
+        eta_inf = fix_eta_inf if fix_eta_inf is not None else np.exp(v["inf"]) * eta0
         return eta0, eta_inf, lam, a, n
 
     def resid(q):
         eta0, eta_inf, lam, a, n = unpack(q)
         return w * (np.log(carreau_yasuda(g, eta0, eta_inf, lam, a, n)) - np.log(y))
 
-    q0 = [np.log(y.max() * 1.2), np.log(1.0 / np.median(g)), 1.0, 0.4]
-    lo = [np.log(y.max() * 0.5), np.log(1e-2 / g.max()), 0.2, 0.0]
-    hi = [np.log(y.max() * 20.0), np.log(1e3 / g.min()), 3.0, 0.99]
-    if fix_eta_inf is None:
-        q0.append(np.log(0.05))
-        lo.append(np.log(1e-4))
-        hi.append(np.log(0.5))
+    lo_v = np.array([lo[k] for k in free])
+    hi_v = np.array([hi[k] for k in free])
     best = None
     for lam0 in (0.3, 1.0, 3.0):  # a few starts in lambda
-        q = list(q0)
-        q[1] = np.log(lam0 / np.median(g))
-        q = np.clip(q, np.array(lo) + 1e-9, np.array(hi) - 1e-9)
-        r = least_squares(resid, q, bounds=(lo, hi))
+        q = np.array([q0[k] if k != "lam" else np.log(lam0) for k in free])
+        q = np.clip(q, lo_v + 1e-9, hi_v - 1e-9)
+        r = least_squares(resid, q, bounds=(lo_v, hi_v))
         if best is None or r.cost < best.cost:
             best = r
     eta0, eta_inf, lam, a, n = unpack(best.x)

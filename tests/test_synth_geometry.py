@@ -51,6 +51,29 @@ def test_carreau_yasuda_fit_recovers_known_parameters():
     assert abs(flat["eta0"] - 5.0) < 0.05 and abs(R.carreau_yasuda(0.1, flat["eta0"], flat["eta_inf"], flat["lam"], flat["a"], flat["n"]) - 5.0) < 0.05
 
 
+def test_shape_constrained_carreau_yasuda_fit_recovers_lambda():
+    # with a, n and eta_inf pinned to the generating values, the fit of data
+    # drawn from each of the paper's four CY curves (its table, 1 % noise,
+    # the rate windows of the 76 x 76 runs) recovers eta0 and the onset time
+    # lambda; a curve with lambda twice as large gives a fit twice as large
+    from paper_2512_13267_gb300 import rheometry as R
+    rng = np.random.default_rng(4)
+    table = {4: (13.20, 0.0, 23.50, 0.71, 0.60), 8: (34.29, 3.15, 89.75, 0.95, 0.37),
+             16: (173.18, 4.45, 353.48, 0.55, 0.18), 32: (242.83, 4.81, 1307.88, 1.23, 0.29)}
+    rates = {4: [0.002, 0.005, 0.01, 0.02, 0.05, 0.1, 0.2],
+             8: [0.001, 0.002, 0.005, 0.01, 0.02, 0.05, 0.1],
+             16: [0.0005, 0.001, 0.002, 0.005, 0.01, 0.02],
+             32: [0.0002, 0.0005, 0.001, 0.002, 0.005, 0.01]}
+    for nd, (e0, einf, lam, a, n) in table.items():
+        g = np.array(rates[nd])
+        for scale in (1.0, 2.0):
+            eta = R.carreau_yasuda(g, e0, einf, scale * lam, a, n) * (1 + 0.01 * rng.standard_normal(len(g)))
+            fit = R.fit_carreau_yasuda(g, eta, 0.01 * eta, fix_eta_inf=einf, fix_a=a, fix_n=n)
+            assert abs(fit["lam"] / (scale * lam) - 1) < 0.15, (nd, scale, fit)
+            assert abs(fit["eta0"] / e0 - 1) < 0.1, (nd, scale, fit)
+            assert fit["a"] == a and fit["n"] == n and fit["eta_inf"] == einf
+
+
 def test_relaxation_time_from_decay():
     # a fast (0.3) plus a slow (50) exponential mode with noise: the tail fit
     # past the fast decay finds the slow time constant; a single exponential
