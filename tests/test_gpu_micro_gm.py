@@ -189,3 +189,65 @@ def test_device_list_advance_of_large_boxes_equals_plain_advance(afbc_mode):
             assert np.array_equal(np.asarray(x), np.asarray(y))
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("dim,edge,n", [(3, 27.0, 3 * 27 ** 3), (2, 127.0, 64512)])
+def test_largest_supported_boxes_match_oracle(dim, edge, n):
+    # the size limits of the engine (16-bit bead and cell ids): a 27^3 box of
+    # 59 049 beads and 19 683 cells, and a 127 x 127 2D melt of 64 512 beads
+    # (16 129 cells), both under a velocity gradient through the AFBC shell
+    lh = _lh()
+    L = np.zeros((1, 9), np.float32)
+    L[0, 1] = 0.05
+    if dim == 3:
+        batch = S.make_batch(np.array([edge]), L, 11, flow="afbc", n_beads=np.array([n]))
+        params = lh.dpd_params(flow="afbc", seed=11)
+        op = O.dpd_params(flow_mode=O.FLOW_AFBC, seed=11)
+    else:
+        batch = S.make_batch(np.array([edge]), L, 11, flow="afbc", chain_len=8, fraction=1.0,
+                             n_beads=np.array([n]), dim=2)
+        params = lh.dpd_params(flow="afbc", seed=11, dim=2, **PAPER_2D)
+        op = O.dpd_params(flow_mode=O.FLOW_AFBC, seed=11, dim=2, **PAPER_2D)
+    assert batch.n_beads[0] == n <= 65535
+    m = lh.Micro.from_batch(params, batch)
+    (ob,) = _oracle_boxes(batch, op)
+    _, _, f, _, _ = m.get_state(0)
+    assert np.abs(f - ob.force).max() <= 1e-4
+    Lg = torch.from_numpy(batch.L).cuda()
+    st = torch.zeros((1, 6), dtype=torch.float64, device="cuda")
+    m.advance(Lg, 5, st)
+    assert m.sync(raise_on_error=False)[0] == lh.OK
+    ref, _, err = O.advance(op, ob, batch.L[0], 5)
+    assert err == 0
+    pos, _, _, step, _ = m.get_state(0)
+    assert step == 5
+    assert np.abs(_minimage(pos - ob.pos, edge)).max() <= 1e-3
+    got = st.cpu().numpy()[0]
+    assert np.abs(got - ref).max() <= 2e-2 * (1.0 + np.abs(ref).max()), (got, ref)
+    m.close()
+
+
+def test_boxes_past_the_id_limits_are_rejected_on_the_host():
+    # 65 536 beads, or more than 65 535 cells, do not fit the 16-bit ids: the
+    # handle is refused before anything runs on the device
+    lh = _lh()
+    n = 65536
+    with pytest.raises(lh.LhmmError) as ei:
+        lh.Micro(lh.dpd_params(), np.array([[28.0, 28.0, 28.0]]), np.array([n], np.int32),
+                 np.array([0], np.int32), 10, np.zeros((n, 3)), np.zeros((n, 3)))
+    assert ei.value.status == lh.ERR_ARG
+    n = 1000  # sparse box of 41^3 = 68 921 cells
+    with pytest.raises(lh.LhmmError) as ei:
+        lh.Micro(lh.dpd_params(), np.array([[41.0, 41.0, 41.0]]), np.array([n], np.int32),
+                 np.array([0], np.int32), 10, np.random.default_rng(0).uniform(0, 41, (n, 3)),
+                 np.zeros((n, 3)))
+    assert ei.value.status == lh.ERR_UNSUPPORTED
+    # a Lees-Edwards row stores the x cell offset of its sliding image in
+    # 8 bits: more than 60 cells along x is refused as well
+    n = 400
+    with pytest.raises(lh.LhmmError) as ei:
+        lh.Micro(lh.dpd_params(flow="lees_edwards", dim=2), np.array([[61.0, 10.0, 1.0]]),
+                 np.array([n], np.int32), np.array([0], np.int32), 10,
+                 np.random.default_rng(1).uniform(0, 10, (n, 3)) * [6.1, 1.0, 0.0],
+                 np.zeros((n, 3)))
+    assert ei.value.status == lh.ERR_UNSUPPORTED
