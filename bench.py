@@ -13,6 +13,20 @@ batch of the same shape (weak scaling, no data-path collective).
 --impl reference times the FP64 CPU oracle (the reference arm of this
 build) on a bounded sample of the same workload on the host cores.
 
+Beside the main metric, rank 0 adds these entries to the line.  Each
+comes after the timed region, and a flag skips it:
+  cpu_baseline   the oracle on a 10 s sample of the workload (--no-cpu-baseline)
+  secondary, rpf_paper, rpm_paper
+                 macro-steps/s of the coupled channel, of the paper's
+                 reverse-Poiseuille set-up and of its porous-medium scale
+                 (--no-macro)
+  surrogate      plain vs surrogate-gated channel: closure trained on 1.02M
+                 pairs for 20k steps, gate threshold 0.1 with online
+                 calibration, profile errors and noise floor (about a
+                 minute; --no-surrogate)
+  large_mixed    plain vs gated cylinder array with 16.4M beads, 200 macro
+                 steps each (--no-large-mixed)
+
   python bench.py --profile-case micro|mlp|sph
 
 runs one fixed, small invocation of a kernel family for a profiler to

@@ -133,19 +133,37 @@ def melt_viscosity(chain_len, shear_rates, replicas=32, edge=20.0, equil_time=No
 
 
 def stress_relaxation(chain_len, shear_rate, replicas=64, edge=20.0, shear_time=None,
-                      relax_time=None, sample_time=1.0, seed=13, exclude_bonds=0):
+                      relax_time=None, sample_time=1.0, seed=13, exclude_bonds=0,
+                      rheometer="lees_edwards", afbc_mode=0):
     """Recovery test (Sec. 5.2): steady shear at shear_rate for shear_time,
     then the shear is removed and the replica-averaged pi_xy is recorded in
     windows of sample_time; G(t) = <pi_xy(t)> / gamma with gamma the total
-    applied strain shear_rate * shear_time (the paper's definition)."""
+    applied strain shear_rate * shear_time (the paper's definition).
+    rheometer = "lees_edwards": periodic boxes sheared by sliding images;
+    "afbc": the paper's rheometer, square boxes sheared through the AFBC
+    shell (L_xy = shear_rate, then L = 0, which holds the shell at rest) with
+    the stress of the core."""
     import torch
     dt = PAPER_2D["dt"]
     lam_guess = 23.5 * (chain_len / 4.0) ** 2
     shear_time = max(100.0, 5 * lam_guess) if shear_time is None else shear_time
     relax_time = max(100.0, 5 * lam_guess) if relax_time is None else relax_time
-    batch = synth.melt_rheometer_batch(chain_len, [shear_rate], replicas, edge=edge, seed=seed)
-    params = lhmm.dpd_params(flow="lees_edwards", seed=seed, dim=2, exclude_bonds=exclude_bonds,
-                             **PAPER_2D)
+    if rheometer == "afbc":
+        Lh = np.zeros((replicas, 9), np.float32)
+        Lh[:, 1] = shear_rate
+        n = int(round(synth.DENSITY_PAPER_2D * edge * edge))
+        n -= n % chain_len
+        batch = synth.make_batch(np.full(replicas, edge), Lh, seed, flow="afbc",
+                                 chain_len=chain_len, fraction=1.0, n_beads=np.full(replicas, n),
+                                 dim=2)
+        params = lhmm.dpd_params(flow="afbc", seed=seed, dim=2, exclude_bonds=exclude_bonds,
+                                 afbc_mode=afbc_mode, **PAPER_2D)
+    elif rheometer == "lees_edwards":
+        batch = synth.melt_rheometer_batch(chain_len, [shear_rate], replicas, edge=edge, seed=seed)
+        params = lhmm.dpd_params(flow="lees_edwards", seed=seed, dim=2,
+                                 exclude_bonds=exclude_bonds, **PAPER_2D)
+    else:
+        raise ValueError("rheometer must be 'lees_edwards' or 'afbc'")
     m = lhmm.Micro.from_batch(params, batch)
     L = torch.from_numpy(batch.L).cuda()
     st = torch.zeros((batch.n_boxes, 6), dtype=torch.float64, device="cuda")
@@ -168,7 +186,8 @@ def stress_relaxation(chain_len, shear_rate, replicas=64, edge=20.0, shear_time=
     m.close()
     gamma = shear_rate * n_shear * chunk * dt
     return dict(chain_len=chain_len, shear_rate=shear_rate, replicas=replicas, edge=edge,
-                strain=gamma, steady_pi_xy=float(sheared[3]), t=t, pi_xy=pxy, pi_xy_se=se,
+                rheometer=rheometer, strain=gamma, steady_pi_xy=float(sheared[3]), t=t,
+                pi_xy=pxy, pi_xy_se=se,
                 G=[p / gamma for p in pxy], device_status=status)
 
 

@@ -238,3 +238,17 @@ def test_2d_planar_extension_matches_oracle(parity_report):
     _run_schedule(m, op, boxes, batch, [(L, 25), (np.zeros_like(L), 15)], parity_report,
                   "2D planar extension - rest (AFBC)")
     m.close()
+
+
+def test_2d_afbc_recovery_schedule_matches_oracle(parity_report):
+    # the recovery test in the paper's rheometer (rheometry.stress_relaxation
+    # with rheometer="afbc"): simple shear through the AFBC shell, then
+    # L = 0, which holds the shell at rest while the core relaxes
+    batch = _batch("afbc", 41)
+    L = np.zeros((batch.n_boxes, 9), np.float32)
+    L[:, 1] = np.array([0.05, 0.1, 0.2, 0.3, 0.5], np.float32)[:batch.n_boxes]
+    batch.L[:] = L
+    m, op, boxes = _pair(batch, "afbc", 41)
+    _run_schedule(m, op, boxes, batch, [(L, 25), (np.zeros_like(L), 20)], parity_report,
+                  "2D shear - rest (AFBC recovery)")
+    m.close()
