@@ -293,12 +293,17 @@ def surrogate_vs_plain(warm=20, n_data=150, train_steps=2000, batch=4096, n_eval
     rate_plain = _rate(A, timing_steps)
     rate_gated = _rate(B, timing_steps)
     gs = B.gate_stats()
+    # the ceiling of the gated step on this system: every box trusted, no
+    # audit, so no box runs DPD (SPH substeps, inference and gate only)
+    B.set_gate(1e30, 0, absolute, warmup_steps)
+    rate_ceiling = _rate(B, timing_steps)
     status = [lhmm.status_string(x.micro.sync(raise_on_error=False)[0]) for x in (A, B)]
     last = windows[-1]
     out = dict(
         device_status_plain=status[0], device_status_surrogate=status[1],
         macro_steps_per_s_plain=rate_plain, macro_steps_per_s_surrogate=rate_gated,
         speedup=rate_gated / rate_plain,
+        macro_steps_per_s_no_dpd=rate_ceiling, speedup_ceiling=rate_ceiling / rate_plain,
         stress_error_pxy=last["stress_error_pxy"], stress_error_n1=last["stress_error_n1"],
         dpd_fraction_eval=last["dpd_fraction"],
         dpd_fraction_timed=(gs["dpd_boxes"] - gs0["dpd_boxes"])
@@ -467,12 +472,15 @@ def large_mixed_run(n_fluid=16384, cell=16.0, box_beads=1000, U_o=0.25, c_factor
     g0 = cpl.gate_stats()
     rate_gated = _rate(cpl, timing_steps)
     g1 = cpl.gate_stats()
+    cpl.set_gate(1e30, 0)  # ceiling: every box trusted, none on DPD
+    rate_ceiling = _rate(cpl, min(timing_steps, 50))
     status = lhmm.status_string(micro.sync(raise_on_error=False)[0])
     out = dict(workload="periodic cylinder array: cell %.0f, radius 0.25 cell, %d fluid + %d wall SPH "
                         "particles, %d-bead AFBC boxes (%d beads), k'=%d, M=%d"
                         % (L, n_fluid, n_wall, box_beads, batch.total_beads, k_micro, M),
                macro_steps_per_s_plain=rate_plain, macro_steps_per_s_surrogate=rate_gated,
                speedup=rate_gated / rate_plain,
+               macro_steps_per_s_no_dpd=rate_ceiling, speedup_ceiling=rate_ceiling / rate_plain,
                bead_steps_per_s_plain=rate_plain * batch.total_beads * k_micro,
                dpd_fraction=(g1["dpd_boxes"] - g0["dpd_boxes"])
                / max(1, (g1["gated_steps"] - g0["gated_steps"]) * n_fluid),
