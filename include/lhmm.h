@@ -249,6 +249,18 @@ lhmm_status lhmm_micro_plan(lhmm_micro_t h, int* n_classes, int cap, int* class_
  * call it before capturing advances into a CUDA graph. */
 lhmm_status lhmm_micro_set_variant(lhmm_micro_t h, int cls, int variant);
 
+/* Pin the kernel variant of the launches over a box list (advances with
+ * box_idx_dev, lhmm_micro_advance_dev_count and so the DPD boxes of a gated
+ * coupled step); -1 restores the default: one block per SM with as many
+ * threads as the largest box's shared-memory plan allows (1024, else 512),
+ * so that a few boxes each finish in the fewest clocks, else the
+ * device-memory variant 5.  Returns LHMM_ERR_UNSUPPORTED if the variant does
+ * not hold the largest box.  Results equal a full advance's bit for bit in
+ * positions and velocities; the stress averages equal them to FP32
+ * summation order, and bit for bit when both use the same variant.  Call it
+ * before capturing advances into a CUDA graph. */
+lhmm_status lhmm_micro_set_list_variant(lhmm_micro_t h, int variant);
+
 /* ------------------------------------------------------------------------
  * Macroscale SPH (Sec. 3.2, Eqs. sph_continuity and tait; Sec. 3.4,
  * Eq. macro_micro).  2D periodic box [0,Lx) x [0,Ly); particles 0..n-n_wall-1

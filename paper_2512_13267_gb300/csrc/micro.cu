@@ -1133,6 +1133,18 @@ cudaError_t ensure_gm(lhmm_micro_s* h) {
 // heuristic start: more threads for larger boxes; the autotuner refines it
 int default_variant(int n) { return n <= 1100 ? 0 : (n <= 2600 ? 1 : 2); }
 
+// Variant of the launches over a box list (subset and device-list
+// advances, which a gated coupled step uses for the few boxes it sends to
+// DPD): one box per SM and as many threads as fit, so that a box finishes
+// in the fewest clocks; a box that no shared-memory plan holds runs in the
+// device-memory variant.
+int list_variant(int max_beads, int max_cells, size_t optin) {
+  for (int v : {2, 4, 1, 0, 3})
+    if (micro_smem_bytes(max_beads, max_cells, kVariants[v].threads, kVariants[v].gm) <= optin)
+      return v;
+  return kFirstGmVariant;
+}
+
 void abs_to_rel(const BoxInfo& B, const double* x, float4* out, int n) {
   for (int i = 0; i < n; ++i) {
     int c[3];
@@ -1351,15 +1363,11 @@ extern "C" lhmm_status lhmm_micro_create(const lhmm_dpd_params* params,
   h->total = total;
   h->info = info;
   h->stream = static_cast<cudaStream_t>(stream);
-  h->subset_variant = default_variant(max_beads);
+  h->subset_variant = list_variant(max_beads, max_cells, optin);
   auto fail = [&](lhmm_status s) {
     free_micro(h);
     return s;
   };
-  if (class_smem(max_beads, max_cells, h->subset_variant) > optin) {
-    h->subset_variant = 0;  // fewer warps, smaller queues
-    if (class_smem(max_beads, max_cells, 0) > optin) h->subset_variant = kFirstGmVariant;
-  }
   if (class_smem(max_beads, max_cells, h->subset_variant) > optin) return fail(LHMM_ERR_UNSUPPORTED);
   // size classes: one per distinct bead count, merged down to at most 12
   std::vector<int> order(nb);
@@ -1514,7 +1522,9 @@ extern "C" lhmm_status lhmm_micro_advance_dev_count(lhmm_micro_t h, const float*
   int dev = 0, n_sm = 0;
   LHMM_CK(cudaGetDevice(&dev));
   LHMM_CK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-  const int grid = std::min(max_active, 2 * n_sm);
+  // one persistent block per resident slot: with few active boxes each
+  // lands on an SM of its own
+  const int grid = std::min(max_active, kVariants[h->subset_variant].min_blocks * n_sm);
   LHMM_CK(cudaMemsetAsync(h->work_counter, 0, sizeof(int), s));
   LHMM_CK(launch_subset(h, a, box_idx_dev, grid, s));
   return LHMM_OK;
@@ -1792,6 +1802,16 @@ extern "C" lhmm_status lhmm_micro_plan(lhmm_micro_t h, int* n_classes, int cap, 
     if (class_threads) class_threads[k] = kVariants[c.variant].threads;
     if (class_min_blocks) class_min_blocks[k] = kVariants[c.variant].min_blocks;
   }
+  return LHMM_OK;
+}
+
+extern "C" lhmm_status lhmm_micro_set_list_variant(lhmm_micro_t h, int variant) {
+  if (!h || variant < -1 || variant >= kNumVariants) return LHMM_ERR_ARG;
+  const size_t optin = max_optin_smem();
+  const int v = variant < 0 ? list_variant(h->max_beads, h->max_cells, optin) : variant;
+  if (class_smem(h->max_beads, h->max_cells, v) > optin) return LHMM_ERR_UNSUPPORTED;
+  if (kVariants[v].gm) LHMM_CK(ensure_gm(h));
+  h->subset_variant = v;
   return LHMM_OK;
 }
 

@@ -88,6 +88,7 @@ def lib():
         L.lhmm_micro_diagnostics.argtypes = [vp, vp, vp]
         L.lhmm_micro_plan.argtypes = [vp, _I, C.c_int, _I, _I, _I, _I]
         L.lhmm_micro_set_variant.argtypes = [vp, C.c_int, C.c_int]
+        L.lhmm_micro_set_list_variant.argtypes = [vp, C.c_int]
         L.lhmm_sph_create.argtypes = [C.POINTER(SphParams), _F, _F, vp, C.POINTER(vp)]
         L.lhmm_sph_destroy.argtypes = [vp]
         L.lhmm_sph_step.argtypes = [vp, vp, C.c_int, vp, vp]
@@ -282,6 +283,12 @@ class Micro:
     def set_variant(self, cls, variant):
         check(lib().lhmm_micro_set_variant(self.h, int(cls), int(variant)),
               "lhmm_micro_set_variant")
+
+    def set_list_variant(self, variant=-1):
+        """Kernel variant of the launches over a box list (-1: the default,
+        one block per SM with the most threads that fit)."""
+        check(lib().lhmm_micro_set_list_variant(self.h, int(variant)),
+              "lhmm_micro_set_list_variant")
 
     def info(self):
         nb = C.c_int()

@@ -54,8 +54,14 @@ def test_closure_inputs_hold_gradient_history_and_stress():
 
 
 def test_zero_threshold_gate_equals_plain_step():
+    # the gated step's DPD boxes run in the list launch; pinned to the
+    # variant of the plain step's class plan (these 192-bead boxes start at
+    # 256 threads x 4 blocks, variant 0) it reproduces the plain step bit
+    # for bit, stresses included
     a, ca = _system(seed=9)
     b, cb = _system(seed=9)
+    assert [(p["threads"], p["min_blocks"]) for p in a.micro.plan()] == [(256, 4)]
+    b.micro.set_list_variant(0)
     a.set_closure(ca, threshold=0.0)
     b.set_closure(cb, threshold=0.0)
     a.step(3, use_graph=True)
@@ -68,6 +74,31 @@ def test_zero_threshold_gate_equals_plain_step():
     assert np.array_equal(La, Lb) and np.array_equal(sa, sb)
     st = b.gate_stats()
     assert st["gated_steps"] == 3 and st["dpd_boxes"] == 3 * b.n_boxes
+
+
+def test_default_list_variant_gives_the_plain_step_to_summation_order():
+    # with its default (latency-first) variant the list launch moves every
+    # bead exactly as the class plan does: the fixed-point pair forces do
+    # not depend on the launch shape; the FP32 virial sums may differ in the
+    # last bits, so the coupled fields after three gated steps agree to
+    # rounding
+    a, ca = _system(seed=9)
+    b, cb = _system(seed=9)
+    a.set_closure(ca, threshold=0.0)
+    b.set_closure(cb, threshold=0.0)
+    a.step(3, use_graph=True)
+    b.step(3, use_graph=True)
+    b.enable_gate(True)
+    a.step(1, use_graph=False)
+    b.step(1, use_graph=False)
+    pa = [a.micro.get_state(k)[0] for k in range(a.n_boxes)]
+    pb = [b.micro.get_state(k)[0] for k in range(b.n_boxes)]
+    assert all(np.array_equal(x, y) for x, y in zip(pa, pb))
+    a.step(2, use_graph=True)
+    b.step(2, use_graph=True)
+    La, sa = a.exchange()
+    Lb, sb = b.exchange()
+    assert np.allclose(La, Lb, rtol=1e-4, atol=1e-6) and np.allclose(sa, sb, rtol=1e-4, atol=1e-9)
 
 
 def test_open_gate_freezes_boxes_and_applies_prediction():
