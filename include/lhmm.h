@@ -251,10 +251,14 @@ lhmm_status lhmm_micro_set_variant(lhmm_micro_t h, int cls, int variant);
 
 /* Pin the kernel variant of the launches over a box list (advances with
  * box_idx_dev, lhmm_micro_advance_dev_count and so the DPD boxes of a gated
- * coupled step); -1 restores the default: one block per SM with as many
- * threads as the largest box's shared-memory plan allows (1024, else 512),
- * so that a few boxes each finish in the fewest clocks, else the
- * device-memory variant 5.  Returns LHMM_ERR_UNSUPPORTED if the variant does
+ * coupled step); -1 restores the default, which picks the shape by the
+ * number of listed boxes: up to one box per SM, one block per SM with as
+ * many threads as the largest box's shared-memory plan allows (1024, else
+ * 512), so that each box finishes in the fewest clocks; more boxes, two
+ * blocks of 512 threads per SM where the box fits that plan.  Boxes no
+ * shared-memory plan holds use the device-memory variant 5.  For
+ * lhmm_micro_advance_dev_count the count is on the device, so both launches
+ * are queued and each leaves the boxes to the other outside its range.  Returns LHMM_ERR_UNSUPPORTED if the variant does
  * not hold the largest box.  Results equal a full advance's bit for bit in
  * positions and velocities; the stress averages equal them to FP32
  * summation order, and bit for bit when both use the same variant.  Call it

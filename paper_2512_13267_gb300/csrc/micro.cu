@@ -31,6 +31,7 @@
 // by (min id, max id, step), so it is identical from both sides and across
 // runs, and a checkpointed state resumes bit for bit.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -87,6 +88,7 @@ struct MicroArgs {
   int* work_counter;         // persistent mode: next work item (NULL: one block per item)
   const int* n_items_dev;    // persistent mode: device-side item count
   int max_items;             // persistent mode: capacity of the item list
+  int count_lo, count_hi;    // persistent mode: run only if count_lo < item count <= count_hi
   unsigned char* gm;         // boxes held in global memory: per-box scratch (else NULL)
   size_t gm_stride;          // bytes of scratch per box
 };
@@ -877,13 +879,21 @@ __global__ void __launch_bounds__(T, MINB) micro_kernel(const MicroArgs A) {
 template <int T, int MINB, bool PEC, bool GM>
 __global__ void __launch_bounds__(T, MINB) micro_kernel_persistent(const MicroArgs A) {
   __shared__ int s_item;
-  const int limit = min(*A.n_items_dev, A.max_items);
+  {
+    // a launch shaped for another range of item counts leaves the items to
+    // it (the same test in every thread, before any barrier)
+    const int count = min(*A.n_items_dev, A.max_items);
+    if (count <= A.count_lo || count > A.count_hi) return;
+  }
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(A.work_counter, 1);
+    if (threadIdx.x == 0) {
+      const int item = atomicAdd(A.work_counter, 1);
+      s_item = item < min(*A.n_items_dev, A.max_items) ? item : -1;
+    }
     __syncthreads();
     const int item = s_item;
     __syncthreads();
-    if (item >= limit) return;
+    if (item < 0) return;
     micro_box<T, PEC, GM>(A, A.list[item]);
     __syncthreads();
   }
@@ -1091,7 +1101,8 @@ struct lhmm_micro_s {
   bool all_persistent = false;  // full advances as one persistent launch (autotuner's choice)
   int all_variant = 0;          // its kernel variant
   int* n_all_d = nullptr;       // device copy of n_boxes, its item count
-  int subset_variant = 1;  // single launch over a device-side box list
+  int subset_variant = 1;   // launches over a box list, at most one box per resident slot
+  int list_tp_variant = 1;  // launches over a box list with more boxes than that
   unsigned char* gm = nullptr;  // per-box scratch of the global-memory variants
   size_t gm_stride = 0;
 };
@@ -1143,6 +1154,15 @@ int list_variant(int max_beads, int max_cells, size_t optin) {
     if (micro_smem_bytes(max_beads, max_cells, kVariants[v].threads, kVariants[v].gm) <= optin)
       return v;
   return kFirstGmVariant;
+}
+
+// ... and with more boxes than SMs: two blocks of 512 threads per SM, which
+// measured fastest from one to eight boxes per SM (1000- and 1500-bead
+// boxes), else the latency shape
+int list_tp_variant(int max_beads, int max_cells, size_t optin, int latency_variant) {
+  return micro_smem_bytes(max_beads, max_cells, kVariants[1].threads, kVariants[1].gm) <= optin
+             ? 1
+             : latency_variant;
 }
 
 void abs_to_rel(const BoxInfo& B, const double* x, float4* out, int n) {
@@ -1240,6 +1260,8 @@ MicroArgs make_args(const lhmm_micro_s* h) {
   a.id_base = h->id_base;
   a.gm = h->gm;
   a.gm_stride = h->gm_stride;
+  a.count_lo = -1;
+  a.count_hi = INT_MAX;
   return a;
 }
 
@@ -1282,12 +1304,26 @@ cudaError_t launch_all_persistent(lhmm_micro_s* h, MicroArgs a, cudaStream_t s) 
   return launch_variant(v, a, grid, class_smem(h->max_beads, h->max_cells, v), s);
 }
 
-cudaError_t launch_subset(lhmm_micro_s* h, MicroArgs a, const int* list, int n, cudaStream_t s) {
+cudaError_t launch_list(lhmm_micro_s* h, MicroArgs a, const int* list, int v, int grid,
+                        cudaStream_t s) {
   a.list = list;
   a.max_beads = h->max_beads;
   a.max_cells = h->max_cells;
-  return launch_variant(h->subset_variant, a, n,
-                        class_smem(h->max_beads, h->max_cells, h->subset_variant), s);
+  return launch_variant(v, a, grid, class_smem(h->max_beads, h->max_cells, v), s);
+}
+
+int sm_count() {
+  int dev = 0, n_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  return n_sm > 0 ? n_sm : 1;
+}
+
+// A list of n boxes known on the host: the latency shape while every box
+// can have a resident slot of its own, else the throughput shape.
+cudaError_t launch_subset(lhmm_micro_s* h, MicroArgs a, const int* list, int n, cudaStream_t s) {
+  const int slots = kVariants[h->subset_variant].min_blocks * sm_count();
+  return launch_list(h, a, list, n <= slots ? h->subset_variant : h->list_tp_variant, n, s);
 }
 
 }  // namespace
@@ -1364,6 +1400,7 @@ extern "C" lhmm_status lhmm_micro_create(const lhmm_dpd_params* params,
   h->info = info;
   h->stream = static_cast<cudaStream_t>(stream);
   h->subset_variant = list_variant(max_beads, max_cells, optin);
+  h->list_tp_variant = list_tp_variant(max_beads, max_cells, optin, h->subset_variant);
   auto fail = [&](lhmm_status s) {
     free_micro(h);
     return s;
@@ -1519,14 +1556,25 @@ extern "C" lhmm_status lhmm_micro_advance_dev_count(lhmm_micro_t h, const float*
   a.work_counter = h->work_counter;
   a.n_items_dev = n_active_dev;
   a.max_items = max_active;
-  int dev = 0, n_sm = 0;
-  LHMM_CK(cudaGetDevice(&dev));
-  LHMM_CK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-  // one persistent block per resident slot: with few active boxes each
-  // lands on an SM of its own
-  const int grid = std::min(max_active, kVariants[h->subset_variant].min_blocks * n_sm);
+  const int n_sm = sm_count();
+  // The item count is known only on the device, so two persistent launches
+  // are queued and each leaves the items to the other outside its range:
+  // up to one box per resident slot of the latency shape (each box on an SM
+  // of its own), the throughput shape beyond.
+  const int lat = h->subset_variant, tp = h->list_tp_variant;
+  const int slots = kVariants[lat].min_blocks * n_sm;
   LHMM_CK(cudaMemsetAsync(h->work_counter, 0, sizeof(int), s));
-  LHMM_CK(launch_subset(h, a, box_idx_dev, grid, s));
+  if (lat == tp || max_active <= slots) {
+    LHMM_CK(launch_list(h, a, box_idx_dev, lat,
+                        std::min(max_active, kVariants[lat].min_blocks * n_sm), s));
+    return LHMM_OK;
+  }
+  a.count_hi = slots;
+  LHMM_CK(launch_list(h, a, box_idx_dev, lat, slots, s));
+  a.count_lo = slots;
+  a.count_hi = INT_MAX;
+  LHMM_CK(launch_list(h, a, box_idx_dev, tp,
+                      std::min(max_active, kVariants[tp].min_blocks * n_sm), s));
   return LHMM_OK;
 }
 
@@ -1808,10 +1856,15 @@ extern "C" lhmm_status lhmm_micro_plan(lhmm_micro_t h, int* n_classes, int cap, 
 extern "C" lhmm_status lhmm_micro_set_list_variant(lhmm_micro_t h, int variant) {
   if (!h || variant < -1 || variant >= kNumVariants) return LHMM_ERR_ARG;
   const size_t optin = max_optin_smem();
-  const int v = variant < 0 ? list_variant(h->max_beads, h->max_cells, optin) : variant;
+  int v = variant, tp = variant;
+  if (variant < 0) {
+    v = list_variant(h->max_beads, h->max_cells, optin);
+    tp = list_tp_variant(h->max_beads, h->max_cells, optin, v);
+  }
   if (class_smem(h->max_beads, h->max_cells, v) > optin) return LHMM_ERR_UNSUPPORTED;
-  if (kVariants[v].gm) LHMM_CK(ensure_gm(h));
+  if (kVariants[v].gm || kVariants[tp].gm) LHMM_CK(ensure_gm(h));
   h->subset_variant = v;
+  h->list_tp_variant = tp;
   return LHMM_OK;
 }
 

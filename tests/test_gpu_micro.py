@@ -482,3 +482,40 @@ def test_full_advance_plan_chosen_by_autotune_gives_the_variants_results():
             assert np.array_equal(np.asarray(x), np.asarray(y))
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("count", [0, 10, 152, 153, 200])
+def test_device_list_advance_takes_each_listed_box_once(count):
+    # the device-side count picks between the latency launch (up to one box
+    # per SM) and the throughput launch (more boxes); either way every listed
+    # box advances exactly once and moves as a host-listed subset advance
+    # moves it (fixed-point pair forces: the launch shape does not change a
+    # trajectory)
+    lh = _lh()
+    nb = 256
+    edges = np.full(nb, 3.0)
+    L = S.random_velocity_gradients(nb, 29, rate_range=(0.05, 0.5))
+    batch = S.make_batch(edges, L, 29, flow="afbc")
+    params = lh.dpd_params(flow="afbc", seed=29)
+    a = lh.Micro.from_batch(params, batch)
+    b = lh.Micro.from_batch(params, batch)
+    perm = np.random.default_rng(29).permutation(nb).astype(np.int32)
+    idx = torch.from_numpy(perm).cuda()
+    cnt = torch.tensor([count], dtype=torch.int32, device="cuda")
+    Lg = torch.from_numpy(batch.L).cuda()
+    st_a = torch.zeros((nb, 6), dtype=torch.float64, device="cuda")
+    st_b = torch.zeros_like(st_a)
+    lh.check(lh.lib().lhmm_micro_advance_dev_count(a.h, lh._ptr(Lg), lh._ptr(idx), lh._ptr(cnt), nb,
+                                                   7, lh._ptr(st_a), None, lh._stream_ptr(None)),
+             "lhmm_micro_advance_dev_count")
+    if count > 0:
+        b.advance(Lg, 7, st_b, box_idx_dev=idx[:count].contiguous())
+    assert a.sync(raise_on_error=False)[0] == b.sync(raise_on_error=False)[0] == lh.OK
+    listed = set(perm[:count].tolist())
+    for box in range(nb):
+        pa, va, _, step_a, _ = a.get_state(box)
+        pb, vb, _, step_b, _ = b.get_state(box)
+        assert step_a == step_b == (7 if box in listed else 0), (box, step_a, step_b)
+        assert np.array_equal(pa, pb) and np.array_equal(va, vb)
+    a.close()
+    b.close()
