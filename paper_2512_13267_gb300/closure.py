@@ -360,13 +360,19 @@ def large_mixed_accuracy(n_fluid=16384, cell=16.0, box_beads=1000, U_o=0.25, c_f
                          eta_s=0.1, alpha=0.01, k_micro=50, dt_dpd=0.01, seed=5, warm=20,
                          n_data=60, train_steps=4000, n_eval=100, threshold=0.02,
                          audit_every=50, absolute=False, noise_floor=True, nbins=8,
-                         timing_steps=50, weight_decay=0.0, warmup_steps=-1):
+                         timing_steps=50, weight_decay=0.0, warmup_steps=-1, thresholds=None,
+                         calibrated=False, online_calibration=False, calibration_decay=0.9):
     """Surrogate-gated vs plain on the large mixed workload: two identical
     systems (and, with noise_floor, a third plain one with another seed) run
     the same plain steps; one collects pairs and trains its closure; then all
     run n_eval steps and the time-averaged pi_xy and N1 fields, binned on an
     nbins x nbins grid over the cell (fluid particles), are compared.
-    Returns errors, DPD share and rates."""
+    `thresholds` (a list) runs one evaluation window per gate threshold, in
+    order; `calibrated` holds out the last 10 % of the pairs for the linear
+    recalibration of the ensemble output (`calibrate`); `online_calibration`
+    lets the gate refit that line from its audits every macro step.  The
+    rates are timed at the last threshold.  Returns errors, DPD shares and
+    rates."""
     kw = dict(n_fluid=n_fluid, cell=cell, box_beads=box_beads, U_o=U_o, c_factor=c_factor,
               eta_s=eta_s, alpha=alpha, k_micro=k_micro, dt_dpd=dt_dpd)
     A, sphA, microA, batch, Lc, M, n_wall = _cylinder_system(seed=seed, **kw)
@@ -386,43 +392,63 @@ def large_mixed_accuracy(n_fluid=16384, cell=16.0, box_beads=1000, U_o=0.25, c_f
             sysm.step(warm + n_data, use_graph=True)
     B.step(warm, use_graph=True)
     X, T = collect_pairs(B, n_data, skip=0, absolute=absolute)
-    mean, std, scale = normalization(X, T)
+    n_fit = X.shape[0] if not calibrated else (X.shape[0] * 9 // 10)  # last 10 %: calibration
+    mean, std, scale = normalization(X[:n_fit], T[:n_fit])
     clo.set_normalization(mean, std, scale)
-    _, t_train = train(clo, X, T, train_steps, weight_decay=weight_decay)
+    _, t_train = train(clo, X[:n_fit], T[:n_fit], train_steps, weight_decay=weight_decay)
+    if calibrated:
+        calibrate(clo, X[n_fit:], T[n_fit:], scale)
+    if online_calibration:
+        B.set_online_calibration(True, calibration_decay)
     B.enable_gate(True)
-    g0 = B.gate_stats()
     nf = n_fluid
-    acc = {name: np.zeros((2, nbins * nbins)) for name, _, _ in systems}
-    for _ in range(n_eval):
-        for name, sysm, sph in systems:
-            sysm.step(1, use_graph=True)
-            p = sph.get_state()[0][:nf]
-            _, st = sysm.exchange()
-            ix = np.minimum((p[:, 0] / Lc * nbins).astype(int), nbins - 1)
-            iy = np.minimum((p[:, 1] / Lc * nbins).astype(int), nbins - 1)
-            k = ix + nbins * iy
-            cnt = np.maximum(np.bincount(k, minlength=nbins * nbins), 1)
-            acc[name][0] += np.bincount(k, weights=st[:, 3], minlength=nbins * nbins) / cnt / n_eval
-            acc[name][1] += np.bincount(k, weights=st[:, 0] - st[:, 1],
-                                        minlength=nbins * nbins) / cnt / n_eval
-    g1 = B.gate_stats()
+    windows = []
+    for thr in (thresholds if thresholds else [threshold]):
+        B.set_gate(thr, audit_every, absolute, warmup_steps)
+        g0 = B.gate_stats()
+        acc = {name: np.zeros((2, nbins * nbins)) for name, _, _ in systems}
+        for _ in range(n_eval):
+            for name, sysm, sph in systems:
+                sysm.step(1, use_graph=True)
+                p = sph.get_state()[0][:nf]
+                _, st = sysm.exchange()
+                ix = np.minimum((p[:, 0] / Lc * nbins).astype(int), nbins - 1)
+                iy = np.minimum((p[:, 1] / Lc * nbins).astype(int), nbins - 1)
+                k = ix + nbins * iy
+                cnt = np.maximum(np.bincount(k, minlength=nbins * nbins), 1)
+                acc[name][0] += np.bincount(k, weights=st[:, 3],
+                                            minlength=nbins * nbins) / cnt / n_eval
+                acc[name][1] += np.bincount(k, weights=st[:, 0] - st[:, 1],
+                                            minlength=nbins * nbins) / cnt / n_eval
+        g1 = B.gate_stats()
+        w = dict(threshold=thr,
+                 stress_error_pxy=rel_l2(acc["B"][0], acc["A"][0]),
+                 stress_error_n1=rel_l2(acc["B"][1], acc["A"][1]),
+                 dpd_fraction=(g1["dpd_boxes"] - g0["dpd_boxes"])
+                 / max(1, (g1["gated_steps"] - g0["gated_steps"]) * nf))
+        if noise_floor:
+            w["noise_floor_pxy"] = rel_l2(acc["C"][0], acc["A"][0])
+            w["noise_floor_n1"] = rel_l2(acc["C"][1], acc["A"][1])
+        windows.append(w)
     rate_gated = _rate(B, timing_steps)
     rate_plain = _rate(A, timing_steps)
+    last = windows[-1]
     out = dict(workload="periodic cylinder array, %d fluid + %d wall SPH particles, %d-bead AFBC "
                         "boxes, k'=%d, M=%d" % (n_fluid, n_wall, box_beads, k_micro, M),
-               target="stress" if absolute else "increment", threshold=threshold,
+               target="stress" if absolute else "increment", threshold=last["threshold"],
                train_pairs=int(X.shape[0]), train_steps=train_steps, t_train_s=t_train,
                n_eval=n_eval, nbins=nbins,
-               stress_error_pxy=rel_l2(acc["B"][0], acc["A"][0]),
-               stress_error_n1=rel_l2(acc["B"][1], acc["A"][1]),
-               dpd_fraction=(g1["dpd_boxes"] - g0["dpd_boxes"])
-               / max(1, (g1["gated_steps"] - g0["gated_steps"]) * nf),
+               stress_error_pxy=last["stress_error_pxy"], stress_error_n1=last["stress_error_n1"],
+               dpd_fraction=last["dpd_fraction"],
                macro_steps_per_s_plain=rate_plain, macro_steps_per_s_surrogate=rate_gated,
                speedup=rate_gated / rate_plain,
+               online_calibration=(B.set_online_calibration(-1).tolist()
+                                   if online_calibration else None),
+               windows=windows if len(windows) > 1 else None,
                device_status=lhmm.status_string(microB.sync(raise_on_error=False)[0]))
     if noise_floor:
-        out["noise_floor_pxy"] = rel_l2(acc["C"][0], acc["A"][0])
-        out["noise_floor_n1"] = rel_l2(acc["C"][1], acc["A"][1])
+        out["noise_floor_pxy"] = last["noise_floor_pxy"]
+        out["noise_floor_n1"] = last["noise_floor_n1"]
     for o in objs:
         o.close()
     return out
