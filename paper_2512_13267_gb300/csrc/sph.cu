@@ -13,7 +13,12 @@
 // a 3x3 tensor for its micro-domain.  A group of kGroup lanes shares one
 // particle: each lane takes every kGroup-th slot of the 3x3 neighbour cells
 // in a fixed order, and the group adds its partial sums with a fixed
-// butterfly, so a step is bit-reproducible.
+// butterfly, so a step is bit-reproducible.  A substep is four launches:
+// kicks, drift and binning in one pass (the previous substep's closing half
+// kick folded in), the cell list (one block for systems of up to 8192
+// particles and cells, else scan, scatter and in-cell sort), the density
+// with the per-particle factors of the momentum sum (p/d^2 and pi/d^2), and
+// the forces.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -33,6 +38,11 @@ struct SphArgs {
   float *d, *p;
   const int* wall;
   int *cnt, *start, *perm, *cell_of;
+  // per-particle factors of the momentum sum, written with the density:
+  // p/d^2 and the micro stress over d^2 (xx, xy, yy; zero where a particle
+  // carries none).  NULL where only densities and gradients are wanted.
+  float* pterm;
+  float4* sterm;
 };
 
 __device__ __forceinline__ float kernel_W(int kind, float r, float h, float hinv) {
@@ -93,6 +103,37 @@ __global__ void sph_kick_drift(SphArgs A, float half_dt, int drift) {
   }
 }
 
+// The start of a substep in one pass: n_kicks half kicks with the current
+// acceleration (two when the previous substep's closing half kick is folded
+// in; the same two additions, in the same order, as two separate passes),
+// the drift, then the particle's cell and its count for the cell list.
+__global__ void sph_kick_drift_bin(SphArgs A, float half_dt, int n_kicks, int drift) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= A.n) return;
+  float2 r = A.pos[I];
+  if (!A.wall[I] && (n_kicks > 0 || drift)) {
+    float2 v = A.vel[I];
+    const float2 a = A.acc[I];
+    for (int k = 0; k < n_kicks; ++k) {
+      v.x += half_dt * a.x;
+      v.y += half_dt * a.y;
+    }
+    A.vel[I] = v;
+    if (drift) {
+      r.x += A.dt * v.x;
+      r.y += A.dt * v.y;
+      r.x -= A.Lx * floorf(r.x / A.Lx);
+      r.y -= A.Ly * floorf(r.y / A.Ly);
+      if (r.x >= A.Lx) r.x -= A.Lx;
+      if (r.y >= A.Ly) r.y -= A.Ly;
+      A.pos[I] = r;
+    }
+  }
+  const int c = cell_index(r, A);
+  A.cell_of[I] = c;
+  atomicAdd(&A.cnt[c], 1);
+}
+
 // Counting sort by cell in four launches: bin and count (cnt must be zero on
 // entry), exclusive scan in one block (which clears cnt for use as cursors),
 // scatter, and an ascending-index sort inside each cell, which leaves cnt zero
@@ -105,7 +146,8 @@ __global__ void sph_bin(SphArgs A) {
   atomicAdd(&A.cnt[c], 1);
 }
 
-__global__ void sph_scan(SphArgs A) {
+// exclusive scan of the cell counts into start (one block; clears cnt)
+__device__ __forceinline__ void scan_counts(const SphArgs& A) {
   __shared__ int warp_tot[32];
   const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int per = (A.ncell + T - 1) / T;
@@ -138,6 +180,8 @@ __global__ void sph_scan(SphArgs A) {
   if (tid == 0) A.start[A.ncell] = A.n;
 }
 
+__global__ void sph_scan(SphArgs A) { scan_counts(A); }
+
 __global__ void sph_scatter(SphArgs A) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= A.n) return;
@@ -149,9 +193,7 @@ __global__ void sph_scatter(SphArgs A) {
 // (rank = number of smaller indices) and written back in ascending order;
 // larger cells (far denser than any SPH state) fall back to an insertion
 // sort by lane 0.
-__global__ void sph_cellsort(SphArgs A) {
-  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (c >= A.ncell) return;  // whole warp
+__device__ __forceinline__ void sort_cell(const SphArgs& A, int c, int lane) {
   const int s0 = A.start[c], m = A.start[c + 1] - s0;
   if (m <= 32) {
     const int key = lane < m ? A.perm[s0 + lane] : 0x7fffffff;
@@ -171,6 +213,26 @@ __global__ void sph_cellsort(SphArgs A) {
     }
   }
   if (lane == 0) A.cnt[c] = 0;
+}
+
+__global__ void sph_cellsort(SphArgs A) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (c >= A.ncell) return;  // whole warp
+  sort_cell(A, c, lane);
+}
+
+// Scan, scatter and in-cell sort of a small system in one block: the same
+// cell list as the three launches above, without the gaps between them.
+__global__ void __launch_bounds__(1024) sph_cells_block(SphArgs A) {
+  scan_counts(A);
+  __syncthreads();
+  for (int I = threadIdx.x; I < A.n; I += blockDim.x) {
+    const int c = A.cell_of[I];
+    A.perm[A.start[c] + atomicAdd(&A.cnt[c], 1)] = I;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int c = threadIdx.x >> 5; c < A.ncell; c += nw) sort_cell(A, c, lane);
 }
 
 constexpr int kGroup = 8;  // lanes per particle in the neighbour sums
@@ -204,7 +266,7 @@ __device__ __forceinline__ float group_sum(float v) {
   return v;
 }
 
-__global__ void sph_density(SphArgs A) {
+__global__ void sph_density(SphArgs A, const double* stress) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int I = t / kGroup, g = t % kGroup;
   const bool valid = I < A.n;
@@ -221,7 +283,19 @@ __global__ void sph_density(SphArgs A) {
     A.d[I] = s;
     const float rr = A.mass * s / A.rho0;
     const float r2 = rr * rr, r4 = r2 * r2;
-    A.p[I] = A.c2rho0_7 * (r4 * r2 * rr - 1.f) + A.pb;  // Eq. tait
+    const float p = A.c2rho0_7 * (r4 * r2 * rr - 1.f) + A.pb;  // Eq. tait
+    A.p[I] = p;
+    if (A.pterm) {  // the factors every neighbour's momentum sum reads
+      const float inv = 1.f / (s * s);
+      A.pterm[I] = p * inv;
+      float4 st = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (stress && I < A.n_fluid && !A.wall[I]) {
+        st.x = static_cast<float>(stress[6 * I + 0]) * inv;
+        st.y = static_cast<float>(stress[6 * I + 3]) * inv;
+        st.z = static_cast<float>(stress[6 * I + 1]) * inv;
+      }
+      A.sterm[I] = st;
+    }
   }
 }
 
@@ -234,14 +308,14 @@ __global__ void sph_force(SphArgs A, const double* stress) {
   if (active) {
     ri = A.pos[I];
     const float2 vi = A.vel[I];
-    const float di = A.d[I], pi_ = A.p[I];
-    const float Pi = pi_ / (di * di);
+    const float di = A.d[I];
+    const float Pi = A.pterm[I];
     float sxx = 0.f, sxy = 0.f, syy = 0.f;
-    if (stress && I < A.n_fluid) {
-      const float inv = 1.f / (di * di);
-      sxx = static_cast<float>(stress[6 * I + 0]) * inv;
-      syy = static_cast<float>(stress[6 * I + 1]) * inv;
-      sxy = static_cast<float>(stress[6 * I + 3]) * inv;
+    if (stress) {
+      const float4 si = A.sterm[I];
+      sxx = si.x;
+      sxy = si.y;
+      syy = si.z;
     }
     for_neighbours(A, I, g, [&](int J) {
       if (J == I) return;
@@ -250,7 +324,7 @@ __global__ void sph_force(SphArgs A, const double* stress) {
       const float F = kernel_F(A.kernel, rr, A.hinv);
       if (F == 0.f || rr == 0.f) return;  // e_IJ undefined for coincident particles
       const float dj = A.d[J];
-      const float P = Pi + A.p[J] / (dj * dj);
+      const float P = Pi + A.pterm[J];
       fx += P * F * r.x;
       fy += P * F * r.y;
       const float2 vj = A.vel[J];
@@ -262,13 +336,8 @@ __global__ void sph_force(SphArgs A, const double* stress) {
       fx -= (A.a_visc * vx + A.b_visc * ve * ex) * cv;
       fy -= (A.a_visc * vy + A.b_visc * ve * ey) * cv;
       if (stress) {
-        float jxx = sxx, jxy = sxy, jyy = syy;
-        if (J < A.n_fluid && !A.wall[J]) {
-          const float inv = 1.f / (dj * dj);
-          jxx += static_cast<float>(stress[6 * J + 0]) * inv;
-          jyy += static_cast<float>(stress[6 * J + 1]) * inv;
-          jxy += static_cast<float>(stress[6 * J + 3]) * inv;
-        }
+        const float4 sj = A.sterm[J];  // zero for wall particles
+        const float jxx = sxx + sj.x, jxy = sxy + sj.y, jyy = syy + sj.z;
         fx -= (jxx * r.x + jxy * r.y) * F;
         fy -= (jxy * r.x + jyy * r.y) * F;
       }
@@ -328,13 +397,27 @@ inline int group_grid(int n_items, int threads) {
   return static_cast<int>((static_cast<long long>(n_items) * kGroup + threads - 1) / threads);
 }
 
+// systems whose cell list one block builds (scan, scatter, in-cell sort)
+constexpr int kOneBlockParticles = 8192;
+constexpr int kOneBlockCells = 8192;
+
+// the cell list from the binned counts (cnt is zero again on exit)
+void finish_cells(const SphArgs& a, cudaStream_t s) {
+  const int T = 128;
+  if (a.n <= kOneBlockParticles && a.ncell <= kOneBlockCells) {
+    sph_cells_block<<<1, 1024, 0, s>>>(a);
+    return;
+  }
+  sph_scan<<<1, 1024, 0, s>>>(a);
+  sph_scatter<<<(a.n + T - 1) / T, T, 0, s>>>(a);
+  sph_cellsort<<<static_cast<int>((32LL * a.ncell + T - 1) / T), T, 0, s>>>(a);
+}
+
 // cell list of the current positions (cnt is zero on entry and on exit)
 void build_cells(const SphArgs& a, cudaStream_t s) {
   const int T = 128;
   sph_bin<<<(a.n + T - 1) / T, T, 0, s>>>(a);
-  sph_scan<<<1, 1024, 0, s>>>(a);
-  sph_scatter<<<(a.n + T - 1) / T, T, 0, s>>>(a);
-  sph_cellsort<<<static_cast<int>((32LL * a.ncell + T - 1) / T), T, 0, s>>>(a);
+  finish_cells(a, s);
 }
 
 }  // namespace
@@ -360,15 +443,24 @@ void free_sph(lhmm_sph_t h) {
   cudaFree(h->a.start);
   cudaFree(h->a.perm);
   cudaFree(h->a.cell_of);
+  cudaFree(h->a.pterm);
+  cudaFree(h->a.sterm);
   delete h;
 }
 
-cudaError_t eval_forces(lhmm_sph_s* h, const double* stress, cudaStream_t s) {
+// density and forces once the particles are binned
+cudaError_t forces_after_bin(lhmm_sph_s* h, const double* stress, cudaStream_t s) {
   const int T = h->threads, Gg = group_grid(h->a.n, T);
-  build_cells(h->a, s);
-  sph_density<<<Gg, T, 0, s>>>(h->a);
+  finish_cells(h->a, s);
+  sph_density<<<Gg, T, 0, s>>>(h->a, stress);
   sph_force<<<Gg, T, 0, s>>>(h->a, stress);
   return cudaGetLastError();
+}
+
+cudaError_t eval_forces(lhmm_sph_s* h, const double* stress, cudaStream_t s) {
+  const int T = h->threads;
+  sph_bin<<<(h->a.n + T - 1) / T, T, 0, s>>>(h->a);
+  return forces_after_bin(h, stress, s);
 }
 
 }  // namespace
@@ -423,7 +515,9 @@ extern "C" lhmm_status lhmm_sph_create(const lhmm_sph_params* params, const floa
       (e = cudaMalloc(&a.cnt, sizeof(int) * a.ncell)) != cudaSuccess ||
       (e = cudaMalloc(&a.start, sizeof(int) * (a.ncell + 1))) != cudaSuccess ||
       (e = cudaMalloc(&a.perm, sizeof(int) * n)) != cudaSuccess ||
-      (e = cudaMalloc(&a.cell_of, sizeof(int) * n)) != cudaSuccess) {
+      (e = cudaMalloc(&a.cell_of, sizeof(int) * n)) != cudaSuccess ||
+      (e = cudaMalloc(&a.pterm, sizeof(float) * n)) != cudaSuccess ||
+      (e = cudaMalloc(&a.sterm, sizeof(float4) * n)) != cudaSuccess) {
     a.wall = wall_d;
     free_sph(h);
     return lhmm_cuda_error(e);
@@ -463,15 +557,18 @@ extern "C" lhmm_status lhmm_sph_step(lhmm_sph_t h, const double* stress_dev, int
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int T = h->threads, G = (h->a.n + T - 1) / T;
   const float half = 0.5f * h->p.dt;
+  // substep k: half kick, drift, bin (with substep k-1's closing half kick
+  // folded in), cell list, density, forces; the last closing half kick
+  // after the loop
   for (int k = 0; k < n_substeps; ++k) {
-    sph_kick_drift<<<G, T, 0, s>>>(h->a, half, 1);
-    LHMM_CK(eval_forces(h, stress_dev, s));
-    sph_kick_drift<<<G, T, 0, s>>>(h->a, half, 0);
+    sph_kick_drift_bin<<<G, T, 0, s>>>(h->a, half, k > 0 ? 2 : 1, 1);
+    LHMM_CK(forces_after_bin(h, stress_dev, s));
   }
+  if (n_substeps > 0) sph_kick_drift<<<G, T, 0, s>>>(h->a, half, 0);
   if (L_out_dev) {
     if (n_substeps == 0) {  // density of the current positions
       build_cells(h->a, s);
-      sph_density<<<group_grid(h->a.n, T), T, 0, s>>>(h->a);
+      sph_density<<<group_grid(h->a.n, T), T, 0, s>>>(h->a, nullptr);
     }
     const int Gf = group_grid(h->a.n_fluid, T);
     if (Gf > 0) sph_velgrad<<<Gf, T, 0, s>>>(h->a, L_out_dev);
@@ -602,7 +699,7 @@ extern "C" lhmm_status lhmm_sph_velgrad_noalloc(const lhmm_sph_params* params,
   const int T = 128, G = group_grid(a.n, T), Gf = group_grid(a.n_fluid, T);
   LHMM_CK(cudaMemsetAsync(a.cnt, 0, sizeof(int) * a.ncell, s));
   build_cells(a, s);
-  sph_density<<<G, T, 0, s>>>(a);
+  sph_density<<<G, T, 0, s>>>(a, nullptr);
   if (Gf > 0) sph_velgrad<<<Gf, T, 0, s>>>(a, L_out_dev);
   LHMM_CK(cudaGetLastError());
   return LHMM_OK;
