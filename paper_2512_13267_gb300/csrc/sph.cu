@@ -10,10 +10,10 @@
 // -(pi_I/d_I^2 + pi_J/d_J^2) F_IJ r_IJ, plus the body force; then the second
 // half kick.  After the substeps the velocity gradient of every fluid
 // particle, L_ab = dv_a/dx_b = sum_J (F_IJ/d_J) v_IJ,a r_IJ,b, is exported as
-// a 3x3 tensor for its micro-domain.  A group of kGroup lanes shares one
-// particle: each lane takes every kGroup-th slot of the 3x3 neighbour cells
-// in a fixed order, and the group adds its partial sums with a fixed
-// butterfly, so a step is bit-reproducible.  A substep is four launches:
+// a 3x3 tensor for its micro-domain.  A group of 8 or 16 lanes shares one
+// particle: each lane takes every 8th or 16th slot of the 3x3 neighbour
+// cells, row by row in a fixed order, and the group adds its partial sums
+// with a fixed butterfly, so a step is bit-reproducible.  A substep is four launches:
 // kicks, drift and binning in one pass (the previous substep's closing half
 // kick folded in), the cell list (one block for systems of up to 8192
 // particles and cells, else scan, scatter and in-cell sort), the density
@@ -235,11 +235,17 @@ __global__ void __launch_bounds__(1024) sph_cells_block(SphArgs A) {
   for (int c = threadIdx.x >> 5; c < A.ncell; c += nw) sort_cell(A, c, lane);
 }
 
-constexpr int kGroup = 8;  // lanes per particle in the neighbour sums
+// lanes per particle in the neighbour sums: 16 for small systems (more
+// parallelism where too few particles keep the SMs busy), 8 above
+// kSmallSystem particles (fewer lanes wasted on short slot runs)
+constexpr int kSmallSystem = 8192;
 
-// Visits lane g's share of the 3x3 cell neighbourhood of particle I: the
-// cells in a fixed order, every kGroup-th slot of each starting at g.
-template <typename F>
+// Visits lane g's share of the 3x3 cell neighbourhood of particle I, row by
+// row (dy = -1, 0, 1): the three cells x-1, x, x+1 of a row are consecutive
+// cell indices, so their particles are one run of cell-list slots (two runs
+// where the row wraps around x), and the lane takes every G-th slot of each
+// run starting at g.  The order is fixed, so the sums are bit-reproducible.
+template <int G, typename F>
 __device__ __forceinline__ void for_neighbours(const SphArgs& A, int I, int g, F&& fn) {
   const int c = A.cell_of[I];
   const int cx = c % A.ncx, cy = c / A.ncx;
@@ -247,38 +253,42 @@ __device__ __forceinline__ void for_neighbours(const SphArgs& A, int I, int g, F
     int y = cy + dy;
     y += (y < 0) ? A.ncy : 0;
     y -= (y >= A.ncy) ? A.ncy : 0;
-    for (int dx = -1; dx <= 1; ++dx) {
-      int x = cx + dx;
-      x += (x < 0) ? A.ncx : 0;
-      x -= (x >= A.ncx) ? A.ncx : 0;
-      const int cc = x + A.ncx * y;
-      const int e = A.start[cc + 1];
-      for (int q = A.start[cc] + g; q < e; q += kGroup) fn(A.perm[q]);
+    const int row = A.ncx * y;
+    // runs [a0, a1) and [b0, b1) of cells; the second is empty without wrap
+    int a0 = cx - 1, a1 = cx + 2, b0 = 0, b1 = 0;
+    if (cx == 0) {
+      a0 = A.ncx - 1; a1 = A.ncx; b0 = 0; b1 = 2;
+    } else if (cx == A.ncx - 1) {
+      a0 = cx - 1; a1 = A.ncx; b0 = 0; b1 = 1;
     }
+    for (int q = A.start[row + a0] + g, e = A.start[row + a1]; q < e; q += G) fn(A.perm[q]);
+    for (int q = A.start[row + b0] + g, e = A.start[row + b1]; q < e; q += G) fn(A.perm[q]);
   }
 }
 
-// Sum over the kGroup lanes of a group (every lane of the warp takes part;
+// Sum over the G lanes of a group (every lane of the warp takes part;
 // a + b == b + a exactly, so every lane of the group gets the same bits).
+template <int G>
 __device__ __forceinline__ float group_sum(float v) {
 #pragma unroll
-  for (int o = kGroup / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
+template <int G>
 __global__ void sph_density(SphArgs A, const double* stress) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int I = t / kGroup, g = t % kGroup;
+  const int I = t / G, g = t % G;
   const bool valid = I < A.n;
   float s = 0.f;
   if (valid) {
     const float2 ri = A.pos[I];
-    for_neighbours(A, I, g, [&](int J) {
+    for_neighbours<G>(A, I, g, [&](int J) {
       const float2 r = min_image(ri, A.pos[J], A.Lx, A.Ly);
       s += kernel_W(A.kernel, sqrtf(r.x * r.x + r.y * r.y), A.h, A.hinv);
     });
   }
-  s = group_sum(s);
+  s = group_sum<G>(s);
   if (valid && g == 0) {
     A.d[I] = s;
     const float rr = A.mass * s / A.rho0;
@@ -299,9 +309,10 @@ __global__ void sph_density(SphArgs A, const double* stress) {
   }
 }
 
+template <int G>
 __global__ void sph_force(SphArgs A, const double* stress) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int I = t / kGroup, g = t % kGroup;
+  const int I = t / G, g = t % G;
   const bool active = I < A.n && !A.wall[I];
   float fx = 0.f, fy = 0.f;
   float2 ri = make_float2(0.f, 0.f);
@@ -317,7 +328,7 @@ __global__ void sph_force(SphArgs A, const double* stress) {
       sxy = si.y;
       syy = si.z;
     }
-    for_neighbours(A, I, g, [&](int J) {
+    for_neighbours<G>(A, I, g, [&](int J) {
       if (J == I) return;
       const float2 r = min_image(ri, A.pos[J], A.Lx, A.Ly);
       const float rr = sqrtf(r.x * r.x + r.y * r.y);
@@ -343,8 +354,8 @@ __global__ void sph_force(SphArgs A, const double* stress) {
       }
     });
   }
-  fx = group_sum(fx);
-  fy = group_sum(fy);
+  fx = group_sum<G>(fx);
+  fy = group_sum<G>(fy);
   if (I < A.n && g == 0) {
     if (!active) {
       A.acc[I] = make_float2(0.f, 0.f);  // wall particles stay fixed
@@ -359,14 +370,15 @@ __global__ void sph_force(SphArgs A, const double* stress) {
   }
 }
 
+template <int G>
 __global__ void sph_velgrad(SphArgs A, float* L_out) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int I = t / kGroup, g = t % kGroup;
+  const int I = t / G, g = t % G;
   const bool valid = I < A.n_fluid;
   float Lxx = 0.f, Lxy = 0.f, Lyx = 0.f, Lyy = 0.f;
   if (valid) {
     const float2 ri = A.pos[I], vi = A.vel[I];
-    for_neighbours(A, I, g, [&](int J) {
+    for_neighbours<G>(A, I, g, [&](int J) {
       if (J == I) return;
       const float2 r = min_image(ri, A.pos[J], A.Lx, A.Ly);
       const float F = kernel_F(A.kernel, sqrtf(r.x * r.x + r.y * r.y), A.hinv);
@@ -380,10 +392,10 @@ __global__ void sph_velgrad(SphArgs A, float* L_out) {
       Lyy += cf * vy * r.y;
     });
   }
-  Lxx = group_sum(Lxx);
-  Lxy = group_sum(Lxy);
-  Lyx = group_sum(Lyx);
-  Lyy = group_sum(Lyy);
+  Lxx = group_sum<G>(Lxx);
+  Lxy = group_sum<G>(Lxy);
+  Lyx = group_sum<G>(Lyx);
+  Lyy = group_sum<G>(Lyy);
   if (valid && g == 0) {
     float* o = L_out + 9 * I;
     o[0] = Lxx; o[1] = Lxy; o[2] = 0.f;
@@ -392,9 +404,26 @@ __global__ void sph_velgrad(SphArgs A, float* L_out) {
   }
 }
 
-// grid for one group of kGroup lanes per item
-inline int group_grid(int n_items, int threads) {
-  return static_cast<int>((static_cast<long long>(n_items) * kGroup + threads - 1) / threads);
+// grid for one group of G lanes per item
+inline int group_grid(int n_items, int threads, int G) {
+  return static_cast<int>((static_cast<long long>(n_items) * G + threads - 1) / threads);
+}
+
+// the neighbour sums with their group sizes (densities always 16 lanes a
+// particle; forces and gradients 16 in small systems, else 8)
+void launch_density(const SphArgs& a, const double* stress, int T, cudaStream_t s) {
+  sph_density<16><<<group_grid(a.n, T, 16), T, 0, s>>>(a, stress);
+}
+
+void launch_force(const SphArgs& a, const double* stress, int T, cudaStream_t s) {
+  if (a.n <= kSmallSystem) sph_force<16><<<group_grid(a.n, T, 16), T, 0, s>>>(a, stress);
+  else sph_force<8><<<group_grid(a.n, T, 8), T, 0, s>>>(a, stress);
+}
+
+void launch_velgrad(const SphArgs& a, float* L_out, int T, cudaStream_t s) {
+  if (a.n_fluid <= 0) return;
+  if (a.n <= kSmallSystem) sph_velgrad<16><<<group_grid(a.n_fluid, T, 16), T, 0, s>>>(a, L_out);
+  else sph_velgrad<8><<<group_grid(a.n_fluid, T, 8), T, 0, s>>>(a, L_out);
 }
 
 // systems whose cell list one block builds (scan, scatter, in-cell sort)
@@ -450,10 +479,9 @@ void free_sph(lhmm_sph_t h) {
 
 // density and forces once the particles are binned
 cudaError_t forces_after_bin(lhmm_sph_s* h, const double* stress, cudaStream_t s) {
-  const int T = h->threads, Gg = group_grid(h->a.n, T);
   finish_cells(h->a, s);
-  sph_density<<<Gg, T, 0, s>>>(h->a, stress);
-  sph_force<<<Gg, T, 0, s>>>(h->a, stress);
+  launch_density(h->a, stress, h->threads, s);
+  launch_force(h->a, stress, h->threads, s);
   return cudaGetLastError();
 }
 
@@ -568,10 +596,9 @@ extern "C" lhmm_status lhmm_sph_step(lhmm_sph_t h, const double* stress_dev, int
   if (L_out_dev) {
     if (n_substeps == 0) {  // density of the current positions
       build_cells(h->a, s);
-      sph_density<<<group_grid(h->a.n, T), T, 0, s>>>(h->a, nullptr);
+      launch_density(h->a, nullptr, T, s);
     }
-    const int Gf = group_grid(h->a.n_fluid, T);
-    if (Gf > 0) sph_velgrad<<<Gf, T, 0, s>>>(h->a, L_out_dev);
+    launch_velgrad(h->a, L_out_dev, T, s);
   }
   LHMM_CK(cudaGetLastError());
   return LHMM_OK;
@@ -696,11 +723,11 @@ extern "C" lhmm_status lhmm_sph_velgrad_noalloc(const lhmm_sph_params* params,
   a.cnt = ib + 4 * kNoallocMaxParticles;  // zeroed at the start of every call
   a.start = a.cnt + kNoallocMaxCells;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int T = 128, G = group_grid(a.n, T), Gf = group_grid(a.n_fluid, T);
+  const int T = 128;
   LHMM_CK(cudaMemsetAsync(a.cnt, 0, sizeof(int) * a.ncell, s));
   build_cells(a, s);
-  sph_density<<<G, T, 0, s>>>(a, nullptr);
-  if (Gf > 0) sph_velgrad<<<Gf, T, 0, s>>>(a, L_out_dev);
+  launch_density(a, nullptr, T, s);
+  launch_velgrad(a, L_out_dev, T, s);
   LHMM_CK(cudaGetLastError());
   return LHMM_OK;
 }
