@@ -20,10 +20,10 @@ comes after the timed region, and a flag skips it:
                  macro-steps/s of the coupled channel, of the paper's
                  reverse-Poiseuille set-up and of its porous-medium scale
                  (--no-macro)
-  surrogate      plain vs surrogate-gated channel: closure trained on 1.02M
+  surrogate      plain vs surrogate-gated channel: closure trained on 2.05M
                  pairs for 20k steps, gate threshold 0.1 with online
-                 calibration, profile errors and noise floor (about a
-                 minute; --no-surrogate)
+                 calibration, profile errors and noise floor (about two
+                 minutes; --no-surrogate)
   large_mixed    plain vs gated cylinder array with 16.4M beads, 200 macro
                  steps each (--no-large-mixed)
 
@@ -571,13 +571,13 @@ def main():
         line["rpm_paper"] = rpm
     if rank == 0 and not args.no_surrogate and args.uniform_edge <= 0:
         from paper_2512_13267_gb300 import closure
-        r = closure.surrogate_vs_plain(warm=20, n_data=500, train_steps=20000, n_eval=60,
+        r = closure.surrogate_vs_plain(warm=20, n_data=1000, train_steps=20000, n_eval=60,
                                        absolute=True, calibrated=True, weight_decay=0.0,
                                        threshold=0.1, online_calibration=True, noise_floor=True)
         for k in ("profile_pxy_plain", "profile_pxy_surrogate"):
             r.pop(k, None)
         r["metric"] = "LHMM macro-steps/s, surrogate-gated vs plain"
-        r["budget"] = ("500 macro steps of training pairs (1.02M pairs), 20000 AdamW steps, "
+        r["budget"] = ("1000 macro steps of training pairs (2.05M pairs), 20000 AdamW steps, "
                        "stress target, held-out calibration, gate threshold 0.1 with online "
                        "calibration from the audits (2% round-robin), warm-up k' steps for "
                        "boxes that return to DPD")
