@@ -519,3 +519,38 @@ def test_device_list_advance_takes_each_listed_box_once(count):
         assert np.array_equal(pa, pb) and np.array_equal(va, vb)
     a.close()
     b.close()
+
+
+def test_list_variant_pins_and_errors():
+    # a pinned list variant must hold the largest box; out-of-range indices
+    # are argument errors; -1 restores the count-dependent default; every
+    # shape moves the listed boxes identically
+    lh = _lh()
+    edges = np.array([13.0, 6.0, 8.0])  # 6 591 beads: no shared-memory plan holds the box
+    L = S.random_velocity_gradients(3, 31, rate_range=(0.05, 0.5))
+    batch = S.make_batch(edges, L, 31, flow="afbc")
+    params = lh.dpd_params(flow="afbc", seed=31)
+    m = lh.Micro.from_batch(params, batch)
+    for bad in (-2, len(lh.MICRO_VARIANTS)):
+        with pytest.raises(lh.LhmmError) as ei:
+            m.set_list_variant(bad)
+        assert ei.value.status == lh.ERR_ARG
+    for v in (0, 2):  # shared-memory shapes cannot hold it
+        with pytest.raises(lh.LhmmError) as ei:
+            m.set_list_variant(v)
+        assert ei.value.status == lh.ERR_UNSUPPORTED
+    idx = torch.arange(3, dtype=torch.int32, device="cuda")
+    Lg = torch.from_numpy(batch.L).cuda()
+    states = []
+    for v in (-1, 5, 6):  # default (device memory), 512 x 1 and 256 x 2 in device memory
+        mm = lh.Micro.from_batch(params, batch)
+        mm.set_list_variant(v)
+        st = torch.zeros((3, 6), dtype=torch.float64, device="cuda")
+        mm.advance(Lg, 6, st, box_idx_dev=idx)
+        assert mm.sync(raise_on_error=False)[0] == lh.OK
+        states.append([mm.get_state(b)[:2] for b in range(3)])
+        mm.close()
+    for other in states[1:]:
+        for (pa, va), (pb, vb) in zip(states[0], other):
+            assert np.array_equal(pa, pb) and np.array_equal(va, vb)
+    m.close()
