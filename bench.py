@@ -260,7 +260,48 @@ def cpu_oracle_rate(batch, budget_s=20.0, min_s=10.0, chunk_steps=5, n_boxes=24)
     return rate, threads, desc
 
 
-def macro_step_rate(steps=10, warmup=2):
+def cpu_oracle_macro_rate(sph_cfg, batch, eta_s, alpha, k_micro, n_sample=32):
+    """FP64 oracles on the same coupled channel: one macro step of the SPH
+    oracle over every particle (M substeps, density, velocity gradient) and
+    k' DPD steps of the micro oracle (OpenMP over boxes) on a fixed sample of
+    boxes, scaled to all boxes.  Returns (macro-steps/s, threads, description)."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+    M = sph_cfg["substeps"]
+    op = O.sph_params(n=sph_cfg["pos"].shape[0], Lx=sph_cfg["Lx"], Ly=sph_cfg["Ly"],
+                      h=sph_cfg["h"], mass=sph_cfg["mass"], rho0=1.0, c=sph_cfg["c"],
+                      theta_pb=0.1, eta_s=eta_s, zeta_s=0.0, dt=sph_cfg["dt"],
+                      kernel=O.KERNEL_WENDLAND_C2,
+                      visc_coeffs=O.VISC_DERIVED_2D, body_force=(sph_cfg["body_force"], 0.0),
+                      body_mode=O.BODY_REVERSE_POISEUILLE)
+    pos = sph_cfg["pos"].astype(np.float64)
+    vel = sph_cfg["vel"].astype(np.float64)
+    t0 = time.perf_counter()
+    acc, _ = O.sph_accel(op, pos, vel)
+    O.sph_steps(op, pos, vel, acc, M)
+    d = O.sph_density(op, pos)
+    O.sph_velgrad(op, pos, vel, d)
+    t_sph = time.perf_counter() - t0
+    par = O.dpd_params(flow_mode=O.FLOW_AFBC, seed=3, alpha=alpha)
+    ids = np.arange(min(n_sample, batch.n_boxes))
+    boxes = []
+    for b in ids:
+        sl = batch.box_slice(int(b))
+        ob = O.Box(batch.edges[b], batch.pos[sl], batch.vel[sl], int(batch.n_chains[b]),
+                   batch.chain_len, box_id=int(b))
+        O.compute_forces(par, ob, np.zeros(9))
+        boxes.append(ob)
+    threads = O.max_threads()
+    t0 = time.perf_counter()
+    O.advance_batch(par, boxes, np.zeros((len(ids), 9)), k_micro, n_threads=threads)
+    t_micro = (time.perf_counter() - t0) * batch.n_boxes / len(ids)
+    desc = ("SPH oracle: one macro step of all %d particles (%d substeps, %.1f s); micro "
+            "oracle: %d of %d boxes for %d DPD steps, scaled to all boxes (%.1f s)"
+            % (pos.shape[0], M, t_sph, len(ids), batch.n_boxes, k_micro, t_micro))
+    return 1.0 / (t_sph + t_micro), threads, desc
+
+
+def macro_step_rate(steps=10, warmup=2, cpu_oracle=False):
     """LHMM macro-steps/s of the coupled reverse-Poiseuille channel (64 x 32 SPH
     particles, one 1500-bead AFBC box each, k' = 50 DPD steps per macro step,
     M SPH substeps from the CFL rule), graph-captured macro steps."""
@@ -303,6 +344,10 @@ def macro_step_rate(steps=10, warmup=2):
     cpl.close()
     micro.close()
     sph.close()
+    if cpu_oracle:
+        rate, threads, desc = cpu_oracle_macro_rate(sph_cfg, batch, eta_s, alpha, k_micro)
+        out["cpu_baseline"] = {"value": rate, "unit": "macro-steps/s", "cores": threads,
+                               "kind": "oracle", "sample": desc}
     return out
 
 
@@ -558,7 +603,7 @@ def main():
     if world > 1 and not args.no_macro and args.uniform_edge <= 0:
         line["coupled_sharded"] = sharded_macro_rate(world, rank)
     if rank == 0 and not args.no_macro and args.uniform_edge <= 0:
-        line["secondary"] = macro_step_rate()
+        line["secondary"] = macro_step_rate(cpu_oracle=not args.no_cpu_baseline)
         from paper_2512_13267_gb300 import flows
         line["rpf_paper"] = flows.rpf_paper_rate()
         # the paper's largest run (random porous medium, 76 x 76 boxes of
