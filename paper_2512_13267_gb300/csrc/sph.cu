@@ -221,6 +221,108 @@ __global__ void sph_cellsort(SphArgs A) {
   sort_cell(A, c, lane);
 }
 
+// The start of a substep of a small system in one block, with the cell
+// list built in shared memory: the half kicks and drift of
+// sph_kick_drift_bin (same arithmetic), then count, exclusive scan, scatter
+// and in-cell sort by particle index, the same cell list as the launches
+// above; start and perm are copied out for the neighbour sums, and the
+// global counters are not touched (they stay zero).
+__global__ void __launch_bounds__(1024) sph_substep_cells_block(SphArgs A, float half_dt,
+                                                                int n_kicks, int drift) {
+  extern __shared__ int sm[];
+  int* cnt = sm;                      // ncell counters, then cursors
+  int* start = cnt + A.ncell;         // ncell + 1 cell starts
+  int* perm = start + A.ncell + 1;    // n slots
+  __shared__ int warp_tot[32];
+  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+  for (int c = tid; c < A.ncell; c += T) cnt[c] = 0;
+  __syncthreads();
+  for (int I = tid; I < A.n; I += T) {
+    float2 r = A.pos[I];
+    if (!A.wall[I] && (n_kicks > 0 || drift)) {
+      float2 v = A.vel[I];
+      const float2 a = A.acc[I];
+      for (int k = 0; k < n_kicks; ++k) {
+        v.x += half_dt * a.x;
+        v.y += half_dt * a.y;
+      }
+      A.vel[I] = v;
+      if (drift) {
+        r.x += A.dt * v.x;
+        r.y += A.dt * v.y;
+        r.x -= A.Lx * floorf(r.x / A.Lx);
+        r.y -= A.Ly * floorf(r.y / A.Ly);
+        if (r.x >= A.Lx) r.x -= A.Lx;
+        if (r.y >= A.Ly) r.y -= A.Ly;
+        A.pos[I] = r;
+      }
+    }
+    const int c = cell_index(r, A);
+    A.cell_of[I] = c;
+    atomicAdd(&cnt[c], 1);
+  }
+  __syncthreads();
+  // exclusive scan of the counts (each thread a contiguous range of cells)
+  const int per = (A.ncell + T - 1) / T;
+  const int c0 = min(tid * per, A.ncell), c1 = min(c0 + per, A.ncell);
+  int local = 0;
+  for (int c = c0; c < c1; ++c) local += cnt[c];
+  int x = local;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int y = lane < nw ? warp_tot[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int z = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += z;
+    }
+    if (lane < nw) warp_tot[lane] = y;
+  }
+  __syncthreads();
+  int run = (warp > 0 ? warp_tot[warp - 1] : 0) + x - local;
+  for (int c = c0; c < c1; ++c) {
+    start[c] = run;
+    run += cnt[c];
+    cnt[c] = 0;
+  }
+  if (tid == 0) start[A.ncell] = A.n;
+  __syncthreads();
+  for (int I = tid; I < A.n; I += T) {
+    const int c = A.cell_of[I];
+    perm[start[c] + atomicAdd(&cnt[c], 1)] = I;
+  }
+  __syncthreads();
+  // ascending particle index inside each cell: one warp per cell
+  for (int c = warp; c < A.ncell; c += nw) {
+    const int s0 = start[c], m = start[c + 1] - s0;
+    if (m <= 32) {
+      const int key = lane < m ? perm[s0 + lane] : 0x7fffffff;
+      int rank = 0;
+      for (int t = 0; t < m; ++t) rank += __shfl_sync(0xffffffffu, key, t) < key;
+      __syncwarp();
+      if (lane < m) perm[s0 + rank] = key;
+    } else if (lane == 0) {
+      for (int q = s0 + 1; q < s0 + m; ++q) {
+        const int key = perm[q];
+        int k = q - 1;
+        while (k >= s0 && perm[k] > key) {
+          perm[k + 1] = perm[k];
+          --k;
+        }
+        perm[k + 1] = key;
+      }
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int c = tid; c <= A.ncell; c += T) A.start[c] = start[c];
+  for (int q = tid; q < A.n; q += T) A.perm[q] = perm[q];
+}
+
 // Scan, scatter and in-cell sort of a small system in one block: the same
 // cell list as the three launches above, without the gaps between them.
 __global__ void __launch_bounds__(1024) sph_cells_block(SphArgs A) {
@@ -477,18 +579,36 @@ void free_sph(lhmm_sph_t h) {
   delete h;
 }
 
-// density and forces once the particles are binned
-cudaError_t forces_after_bin(lhmm_sph_s* h, const double* stress, cudaStream_t s) {
-  finish_cells(h->a, s);
+bool one_block_cells(const SphArgs& a) {
+  return a.n <= kOneBlockParticles && a.ncell <= kOneBlockCells;
+}
+
+size_t one_block_smem(const SphArgs& a) {
+  return sizeof(int) * (2 * static_cast<size_t>(a.ncell) + 1 + static_cast<size_t>(a.n));
+}
+
+// the start of a substep: n_kicks half kicks, the drift if asked, and the
+// cell list of the new positions (one block for small systems)
+void substep_start(const SphArgs& a, float half_dt, int n_kicks, int drift, int T,
+                   cudaStream_t s) {
+  if (one_block_cells(a)) {
+    sph_substep_cells_block<<<1, 1024, one_block_smem(a), s>>>(a, half_dt, n_kicks, drift);
+    return;
+  }
+  sph_kick_drift_bin<<<(a.n + T - 1) / T, T, 0, s>>>(a, half_dt, n_kicks, drift);
+  finish_cells(a, s);
+}
+
+// density and forces on the current cell list
+cudaError_t forces_on_cells(lhmm_sph_s* h, const double* stress, cudaStream_t s) {
   launch_density(h->a, stress, h->threads, s);
   launch_force(h->a, stress, h->threads, s);
   return cudaGetLastError();
 }
 
 cudaError_t eval_forces(lhmm_sph_s* h, const double* stress, cudaStream_t s) {
-  const int T = h->threads;
-  sph_bin<<<(h->a.n + T - 1) / T, T, 0, s>>>(h->a);
-  return forces_after_bin(h, stress, s);
+  substep_start(h->a, 0.f, 0, 0, h->threads, s);
+  return forces_on_cells(h, stress, s);
 }
 
 }  // namespace
@@ -560,6 +680,12 @@ extern "C" lhmm_status lhmm_sph_create(const lhmm_sph_params* params, const floa
     vel[I] = wall[I] ? make_float2(0.f, 0.f) : make_float2(vel0_host[2 * I], vel0_host[2 * I + 1]);
   }
   cudaStream_t s = h->stream;
+  if (one_block_cells(a) && one_block_smem(a) > 48 * 1024 &&
+      (e = cudaFuncSetAttribute(sph_substep_cells_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(one_block_smem(a)))) != cudaSuccess) {
+    free_sph(h);
+    return lhmm_cuda_error(e);
+  }
   if ((e = cudaMemcpyAsync(a.pos, pos.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(a.vel, vel.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(wall_d, wall.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
@@ -589,8 +715,8 @@ extern "C" lhmm_status lhmm_sph_step(lhmm_sph_t h, const double* stress_dev, int
   // folded in), cell list, density, forces; the last closing half kick
   // after the loop
   for (int k = 0; k < n_substeps; ++k) {
-    sph_kick_drift_bin<<<G, T, 0, s>>>(h->a, half, k > 0 ? 2 : 1, 1);
-    LHMM_CK(forces_after_bin(h, stress_dev, s));
+    substep_start(h->a, half, k > 0 ? 2 : 1, 1, T, s);
+    LHMM_CK(forces_on_cells(h, stress_dev, s));
   }
   if (n_substeps > 0) sph_kick_drift<<<G, T, 0, s>>>(h->a, half, 0);
   if (L_out_dev) {
