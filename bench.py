@@ -27,13 +27,14 @@ comes after the timed region, and a flag skips it:
   large_mixed    plain vs gated cylinder array with 16.4M beads, 200 macro
                  steps each (--no-large-mixed)
 
-  python bench.py --profile-case micro|mlp|sph
+  python bench.py --profile-case micro|mlp|sph|gated
 
 runs one fixed, small invocation of a kernel family for a profiler to
 capture and exits 0 without a bench line: micro = 304 boxes of edge 12
 (5184 beads) for 3 calls of 10 DPD steps; mlp = 4 closure training steps at
 B = 4096 and one inference of 16 384 rows; sph = 3 x 20 substeps of a
-cylinder cell with 16 384 fluid particles.
+cylinder cell with 16 384 fluid particles; gated = 3 surrogate-gated macro
+steps of the coupled channel with 1 in 14 boxes on DPD.
 """
 import ctypes
 import argparse
@@ -155,7 +156,28 @@ def profile_case_sph(n_fluid=16384, cell=16.0, substeps=20):
     s.close()
 
 
-PROFILE_CASES = {"micro": profile_case_micro, "mlp": profile_case_mlp, "sph": profile_case_sph}
+def profile_case_gated(audit_every=14, steps=3):
+    """Gated macro steps of the coupled channel (2048 particles, 1500-bead
+    boxes): every box trusted by a closure whose increments are negligible,
+    so the flow is the plain one and the DPD share is the audit share
+    (1/audit_every); plain warm-up steps for the gradient history, then
+    `steps` gated steps launched eagerly."""
+    import torch
+    from paper_2512_13267_gb300 import closure as CL
+    kw = dict(alpha=0.01, U_o=0.25, c_factor=10.0, eta_s=0.1, k_micro=50, dt_dpd=0.01, members=5)
+    cpl, clo, _, _ = CL._channel(seed=3, closure_seed=7, **kw)
+    clo.set_normalization(np.zeros(CL.N_IN), np.ones(CL.N_IN), np.full(CL.N_OUT, 1e-9))
+    cpl.set_closure(clo, threshold=1e30, audit_every=audit_every)
+    cpl.step(17, use_graph=False)
+    cpl.enable_gate(True)
+    cpl.step(steps, use_graph=False)
+    torch.cuda.synchronize()
+    for o in (cpl, cpl.micro, cpl.sph, clo):
+        o.close()
+
+
+PROFILE_CASES = {"micro": profile_case_micro, "mlp": profile_case_mlp, "sph": profile_case_sph,
+                 "gated": profile_case_gated}
 
 
 def _peaks():
