@@ -285,8 +285,9 @@ class Micro:
               "lhmm_micro_set_variant")
 
     def set_list_variant(self, variant=-1):
-        """Kernel variant of the launches over a box list (-1: the default,
-        one block per SM with the most threads that fit)."""
+        """Kernel variant of the launches over a box list.  -1 restores the
+        default: up to one listed box per SM, one block per SM with the most
+        threads that fit; more boxes, two 512-thread blocks per SM."""
         check(lib().lhmm_micro_set_list_variant(self.h, int(variant)),
               "lhmm_micro_set_list_variant")
 
