@@ -341,6 +341,7 @@ __global__ void __launch_bounds__(1024) sph_cells_block(SphArgs A) {
 // parallelism where too few particles keep the SMs busy), 8 above
 // kSmallSystem particles (fewer lanes wasted on short slot runs)
 constexpr int kSmallSystem = 8192;
+constexpr int kTinySystem = 4096;  // a whole warp per particle up to here
 
 // Visits lane g's share of the 3x3 cell neighbourhood of particle I, row by
 // row (dy = -1, 0, 1): the three cells x-1, x, x+1 of a row are consecutive
@@ -514,17 +515,20 @@ inline int group_grid(int n_items, int threads, int G) {
 // the neighbour sums with their group sizes (densities always 16 lanes a
 // particle; forces and gradients 16 in small systems, else 8)
 void launch_density(const SphArgs& a, const double* stress, int T, cudaStream_t s) {
-  sph_density<16><<<group_grid(a.n, T, 16), T, 0, s>>>(a, stress);
+  if (a.n <= kTinySystem) sph_density<32><<<group_grid(a.n, T, 32), T, 0, s>>>(a, stress);
+  else sph_density<16><<<group_grid(a.n, T, 16), T, 0, s>>>(a, stress);
 }
 
 void launch_force(const SphArgs& a, const double* stress, int T, cudaStream_t s) {
-  if (a.n <= kSmallSystem) sph_force<16><<<group_grid(a.n, T, 16), T, 0, s>>>(a, stress);
+  if (a.n <= kTinySystem) sph_force<32><<<group_grid(a.n, T, 32), T, 0, s>>>(a, stress);
+  else if (a.n <= kSmallSystem) sph_force<16><<<group_grid(a.n, T, 16), T, 0, s>>>(a, stress);
   else sph_force<8><<<group_grid(a.n, T, 8), T, 0, s>>>(a, stress);
 }
 
 void launch_velgrad(const SphArgs& a, float* L_out, int T, cudaStream_t s) {
   if (a.n_fluid <= 0) return;
-  if (a.n <= kSmallSystem) sph_velgrad<16><<<group_grid(a.n_fluid, T, 16), T, 0, s>>>(a, L_out);
+  if (a.n <= kTinySystem) sph_velgrad<32><<<group_grid(a.n_fluid, T, 32), T, 0, s>>>(a, L_out);
+  else if (a.n <= kSmallSystem) sph_velgrad<16><<<group_grid(a.n_fluid, T, 16), T, 0, s>>>(a, L_out);
   else sph_velgrad<8><<<group_grid(a.n_fluid, T, 8), T, 0, s>>>(a, L_out);
 }
 
